@@ -1,0 +1,253 @@
+"""FP64 CPU oracle for the image-plane dispersed-transient search.
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+cpu_baseline / reference leg of bench.py may import this module.  The product
+path (the CUDA library and its Python binding) never imports or calls it, and
+this module imports nothing from the product.
+
+Plain, slow, obviously correct NumPy float64 code, one function per step of the
+method, each citing the passage of Ruhe et al. (arXiv 2103.15418) it follows:
+
+  delay_table      Sec. 3.2, dispersion delay t_nu = t0 + C_DM DM (nu^-2 - nu0^-2)
+  dedisperse       App. B.2, "perfect dedispersion": sum over subbands after the shift
+  local_centre     Sec. 2.1.1, C := G * X with the uniform kernel, normalised (Z)
+  local_spread     Sec. 2.1.1, S := G * (X - C)^2, square taken element-wise first
+  snr_map          Sec. 2.1.1, threshold y = I(x > c + kappa sqrt(s)) written as S/N
+  local_max_mask   Sec. 2.1.2, q = I(x = max over the (2k+1)^2 window), here k = 1
+  detect           Sec. 2.1.2, p = q AND y
+  frame_stats      mean / RMS of S/N over valid pixels (diagnostic noise level)
+  dynspec          Sec. 2.2, flux measurement + backward fill from cached images
+
+Readings where the paper is silent or garbled (all listed in the design doc):
+  * C_DM = 4.148808e3 s MHz^2 cm^3 / pc (the printed unit "ms" is garbled; with
+    nu in MHz the delay is in seconds); nu_ref = the highest frequency, so every
+    delay is >= 0; delays are rounded half up, floor(x + 0.5), in FP64.
+  * The kernel is the square uniform box of radius r, truncated at the image
+    edge and normalised by the number of in-image pixels (Z of Sec. 2.1.1).
+  * The spread is two-pass: (D - C)^2 uses C at each window pixel.
+  * The local maximum is taken on the dedispersed image over the 3x3 window
+    clipped to the image; ties count as maxima (x = max).
+  * Strict threshold (snr > kappa); pixels with S = 0 are never candidates and
+    carry snr = 0.
+  * A candidate's t0 is its arrival frame at nu_ref; it is produced by the push
+    of frame T = t0 + max_f delay[d][f].
+
+Functions with no independent pin: none (see tests/test_oracle_pins.py).
+"""
+from __future__ import annotations
+
+import math
+from typing import Callable, Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+# Sec. 3.2: C_DM = e^2 pc / (8 pi^2 eps0 m_e c) * 1e-6, in s MHz^2 cm^3 / pc.
+C_DM_S = 4.148808e3
+
+FrameFn = Callable[[int], np.ndarray]   # t -> [F, H, W] float64
+
+
+# --------------------------------------------------------------------- a1
+def delay_table(freqs_mhz: Sequence[float], dm_grid: Sequence[float],
+                cadence_s: float) -> np.ndarray:
+    """Integer delay in frames of subband f for DM trial d (Sec. 3.2, t_nu equation).
+
+    delay[d][f] = floor(C_DM * DM_d * (nu_f^-2 - nu_ref^-2) / cadence + 1/2),
+    nu_ref = max_f nu_f.  Returned as int64 [n_dm, F].
+    """
+    freqs = [float(v) for v in freqs_mhz]
+    ref = max(freqs)
+    out = np.zeros((len(dm_grid), len(freqs)), dtype=np.int64)
+    for d, dm in enumerate(dm_grid):
+        for f, nu in enumerate(freqs):
+            seconds = C_DM_S * float(dm) * (nu ** -2 - ref ** -2)
+            out[d, f] = math.floor(seconds / cadence_s + 0.5)
+    return out
+
+
+def delay_fraction_margin(freqs_mhz, dm_grid, cadence_s) -> float:
+    """Smallest distance of an unrounded delay (in frames) to a rounding tie (.5)."""
+    freqs = np.asarray(freqs_mhz, np.float64)
+    ref = freqs.max()
+    x = C_DM_S * np.asarray(dm_grid, np.float64)[:, None] * (freqs[None] ** -2 - ref ** -2) / cadence_s
+    return float(np.min(np.abs((x - np.floor(x)) - 0.5)))
+
+
+# --------------------------------------------------------------------- a3
+def dedisperse(frame_at: FrameFn, T: int, delays: np.ndarray, d: int) -> Tuple[int, np.ndarray]:
+    """Shift-and-sum for DM trial d completed by frame T (App. B.2, un-normalised mean).
+
+    D_d = sum_f X_f(t0 + delay[d][f]),  t0 = T - max_f delay[d][f].
+    Returns (t0, D) with D float64 [H, W].
+    """
+    row = delays[d]
+    t0 = T - int(row.max())
+    D = None
+    for f in range(len(row)):
+        plane = np.asarray(frame_at(t0 + int(row[f]))[f], dtype=np.float64)
+        D = plane.copy() if D is None else D + plane
+    return t0, D
+
+
+def abs_sum(frame_at: FrameFn, T: int, delays: np.ndarray, d: int) -> np.ndarray:
+    """sum_f |X_f(t0 + delay[d][f])|: scale of the FP32 rounding error of D_d."""
+    row = delays[d]
+    t0 = T - int(row.max())
+    acc = None
+    for f in range(len(row)):
+        plane = np.abs(np.asarray(frame_at(t0 + int(row[f]))[f], dtype=np.float64))
+        acc = plane if acc is None else acc + plane
+    return acc
+
+
+# --------------------------------------------------------------------- a4 / a5
+def window_sum_1d(a: np.ndarray, r: int, axis: int) -> np.ndarray:
+    """sum_{k=-r..r} a[i+k] along one axis, terms outside the array omitted."""
+    a = np.asarray(a, dtype=np.float64)
+    n = a.shape[axis]
+    out = np.zeros_like(a)
+    for k in range(-r, r + 1):
+        dst = [slice(None)] * a.ndim
+        src = [slice(None)] * a.ndim
+        if k >= 0:
+            dst[axis] = slice(0, max(n - k, 0))
+            src[axis] = slice(k, n)
+        else:
+            dst[axis] = slice(-k, n)
+            src[axis] = slice(0, max(n + k, 0))
+        out[tuple(dst)] += a[tuple(src)]
+    return out
+
+
+def box_sum(img: np.ndarray, r: int) -> np.ndarray:
+    """sum over the (2r+1)^2 square window clipped to the image (double sum, rows then columns)."""
+    return window_sum_1d(window_sum_1d(img, r, axis=1), r, axis=0)
+
+
+def window_count(H: int, W: int, r: int) -> np.ndarray:
+    """Number of in-image pixels of each clipped window (the normaliser Z of Sec. 2.1.1)."""
+    return box_sum(np.ones((H, W)), r)
+
+
+def local_centre(D: np.ndarray, r: int) -> np.ndarray:
+    """C := G * D with the uniform box kernel, normalised per pixel (Sec. 2.1.1)."""
+    return box_sum(D, r) / window_count(*D.shape, r)
+
+
+def local_spread(D: np.ndarray, C: np.ndarray, r: int) -> np.ndarray:
+    """S := G * (D - C)^2, the square element-wise before the second filter (Sec. 2.1.1)."""
+    return box_sum((D - C) ** 2, r) / window_count(*D.shape, r)
+
+
+# --------------------------------------------------------------------- a6
+def snr_map(D: np.ndarray, C: np.ndarray, S: np.ndarray) -> np.ndarray:
+    """(D - C)/sqrt(S) where S > 0, else 0 (Sec. 2.1.1 threshold, as S/N)."""
+    out = np.zeros_like(D)
+    ok = S > 0
+    out[ok] = (D[ok] - C[ok]) / np.sqrt(S[ok])
+    return out
+
+
+def neighbour_max(D: np.ndarray) -> np.ndarray:
+    """Max of the 8 neighbours inside the image (-inf where there are none)."""
+    H, W = D.shape
+    pad = np.full((H + 2, W + 2), -np.inf)
+    pad[1:-1, 1:-1] = D
+    best = np.full((H, W), -np.inf)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            if dy == 0 and dx == 0:
+                continue
+            best = np.maximum(best, pad[1 + dy:1 + dy + H, 1 + dx:1 + dx + W])
+    return best
+
+
+def local_max_mask(D: np.ndarray) -> np.ndarray:
+    """q = I(D = max over the 3x3 window clipped to the image) (Sec. 2.1.2, k = 1)."""
+    return D >= neighbour_max(D)
+
+
+def detect(D: np.ndarray, r: int, kappa: float) -> Dict[str, np.ndarray]:
+    """Full per-image chain: C, S, snr, threshold AND local max (Sec. 2.1.1-2.1.2)."""
+    C = local_centre(D, r)
+    S = local_spread(D, C, r)
+    snr = snr_map(D, C, S)
+    above = snr > kappa                     # y: x > c + kappa sqrt(s), S > 0
+    q = local_max_mask(D)
+    return dict(C=C, S=S, snr=snr, valid=S > 0, mask=above & q & (S > 0),
+                lmax_margin=D - neighbour_max(D))
+
+
+# --------------------------------------------------------------------- a7
+def frame_stats(snr: np.ndarray, valid: np.ndarray) -> Tuple[float, float, int]:
+    """(mean, RMS) of S/N over the valid pixels, FP64, and the pixel count."""
+    v = snr[valid]
+    n = int(v.size)
+    if n == 0:
+        return 0.0, 0.0, 0
+    return float(v.sum() / n), float(math.sqrt(float((v * v).sum()) / n)), n
+
+
+# --------------------------------------------------------------------- whole push
+def active_trials(delays: np.ndarray, T: int, T_first: int = 0) -> List[int]:
+    """DM trials whose whole sweep has been pushed by frame T."""
+    dmax = delays.max(axis=1)
+    return [d for d in range(delays.shape[0]) if T - int(dmax[d]) >= T_first]
+
+
+def search_push(frame_at: FrameFn, T: int, delays: np.ndarray, r: int, kappa: float,
+                T_first: int = 0, dms: Optional[Sequence[int]] = None,
+                keep_maps: bool = False):
+    """All candidates (t0, d, y, x, snr) produced by the push of frame T.
+
+    Returns (cands, stats, maps): cands sorted by (t0, d, y, x); stats maps
+    d -> (mean, rms, n); maps (if keep_maps) d -> detect() dict plus D, abs_sum.
+    """
+    cands = []
+    stats = {}
+    maps = {}
+    for d in (active_trials(delays, T, T_first) if dms is None else dms):
+        t0, D = dedisperse(frame_at, T, delays, d)
+        res = detect(D, r, kappa)
+        ys, xs = np.nonzero(res["mask"])
+        for y, x in zip(ys, xs):
+            cands.append((t0, d, int(y), int(x), float(res["snr"][y, x])))
+        stats[d] = frame_stats(res["snr"], res["valid"])
+        if keep_maps:
+            res["D"] = D
+            res["abs_sum"] = abs_sum(frame_at, T, delays, d)
+            res["t0"] = t0
+            maps[d] = res
+    cands.sort(key=lambda c: (c[0], c[1], c[2], c[3]))
+    return cands, stats, maps
+
+
+# --------------------------------------------------------------------- a8
+def dynspec(frame_at: FrameFn, T: int, Tw: int, cands: Sequence[Tuple[int, int]],
+            box_r: int = 0) -> np.ndarray:
+    """Dynamic spectra [n, F, Tw]: the flux at each candidate pixel in the Tw frames
+    ending at T (Sec. 2.2 backward fill); with box_r > 0 the maximum pixel of the
+    (2 box_r + 1)^2 box clipped to the image (Sec. 2.2 flux measurement)."""
+    frames = [np.asarray(frame_at(T - Tw + 1 + tau), np.float64) for tau in range(Tw)]
+    F, H, W = frames[0].shape
+    out = np.zeros((len(cands), F, Tw))
+    for n, (y, x) in enumerate(cands):
+        y0, y1 = max(y - box_r, 0), min(y + box_r + 1, H)
+        x0, x1 = max(x - box_r, 0), min(x + box_r + 1, W)
+        for tau in range(Tw):
+            out[n, :, tau] = frames[tau][:, y0:y1, x0:x1].reshape(F, -1).max(axis=1)
+    return out
+
+
+# --------------------------------------------------------------------- storage
+def storage_round(x: np.ndarray, dtype: str) -> np.ndarray:
+    """Values as stored in a reduced-precision ring (round to nearest even), as float64."""
+    import torch  # plain CPU conversion
+    t = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32))
+    if dtype == "fp32":
+        return t.double().numpy()
+    if dtype == "fp16":
+        return t.to(torch.float16).double().numpy()
+    if dtype == "bf16":
+        return t.to(torch.bfloat16).double().numpy()
+    raise ValueError(dtype)

@@ -1,0 +1,388 @@
+"""Pins of the FP64 oracle against facts independent of its own code.
+
+Each test checks one step of the method against something the paper or the
+mathematics fixes: a physical constant derived from CODATA values, closed forms,
+brute-force loops on tiny inputs, invariants, and the Gaussian false-alarm law
+of App. B.1.  The last group plants plausible mistakes in copies of oracle
+functions and checks that a pin catches each of them.
+"""
+import math
+from decimal import Decimal, getcontext, ROUND_HALF_UP
+
+import numpy as np
+import pytest
+
+from oracle import lpf_oracle as O
+import synth
+
+
+# ----------------------------------------------------------------- helpers
+def brute_box_mean(img, r):
+    H, W = img.shape
+    out = np.zeros((H, W))
+    for y in range(H):
+        for x in range(W):
+            s, n = 0.0, 0
+            for yy in range(y - r, y + r + 1):
+                for xx in range(x - r, x + r + 1):
+                    if 0 <= yy < H and 0 <= xx < W:
+                        s += img[yy, xx]
+                        n += 1
+            out[y, x] = s / n
+    return out
+
+
+def brute_spread(img, C, r):
+    H, W = img.shape
+    out = np.zeros((H, W))
+    for y in range(H):
+        for x in range(W):
+            s, n = 0.0, 0
+            for yy in range(y - r, y + r + 1):
+                for xx in range(x - r, x + r + 1):
+                    if 0 <= yy < H and 0 <= xx < W:
+                        s += (img[yy, xx] - C[yy, xx]) ** 2
+                        n += 1
+            out[y, x] = s / n
+    return out
+
+
+def brute_local_max(img):
+    H, W = img.shape
+    out = np.zeros((H, W), bool)
+    for y in range(H):
+        for x in range(W):
+            m = -math.inf
+            for yy in range(y - 1, y + 2):
+                for xx in range(x - 1, x + 2):
+                    if 0 <= yy < H and 0 <= xx < W:
+                        m = max(m, img[yy, xx])
+            out[y, x] = img[y, x] == m
+    return out
+
+
+def phi(x):
+    return 0.5 * math.erfc(-x / math.sqrt(2.0))
+
+
+# ----------------------------------------------------------------- a1 delay table
+def test_dispersion_constant_from_codata():
+    """Sec. 3.2: C_DM = e^2 pc / (8 pi^2 eps0 m_e c) * 1e-6 (s MHz^2 cm^3/pc)."""
+    e, eps0, me, c = 1.602176634e-19, 8.8541878128e-12, 9.1093837015e-31, 299792458.0
+    pc = 3.0856775814913673e16
+    derived = e ** 2 / (8 * math.pi ** 2 * eps0 * me * c) * pc * 1e-6
+    assert abs(O.C_DM_S - derived) / derived < 1e-6
+    # the paper prints 4148.806 (with a garbled unit)
+    assert abs(O.C_DM_S - 4148.806) < 0.01
+
+
+def test_delay_table_high_precision_rounding():
+    """Same delays from 40-digit decimal arithmetic with round-half-up."""
+    getcontext().prec = 40
+    freqs = synth.AARTFAAC_BANDS
+    dms = np.arange(0, 251, 7, dtype=np.float64)
+    tab = O.delay_table(freqs, dms, 1.0)
+    C = Decimal(repr(O.C_DM_S))
+    ref = Decimal(repr(float(max(freqs))))
+    for d, dm in enumerate(dms):
+        for f, nu in enumerate(freqs):
+            nu = Decimal(repr(float(nu)))
+            x = C * Decimal(repr(float(dm))) * (1 / (nu * nu) - 1 / (ref * ref))
+            assert int(x.quantize(Decimal(1), rounding=ROUND_HALF_UP)) == tab[d, f]
+
+
+def test_delay_table_invariants():
+    freqs = synth.AARTFAAC_BANDS
+    dms = np.arange(251, dtype=np.float64)
+    tab = O.delay_table(freqs, dms, 1.0)
+    ref = int(np.argmax(freqs))
+    assert np.all(tab[:, ref] == 0)                 # no delay at nu_ref
+    assert np.all(tab >= 0)
+    assert np.all(tab[0] == 0)                      # DM 0: no delay
+    assert np.all(np.diff(tab, axis=0) >= 0)        # monotone in DM
+    order = np.argsort(freqs)                       # lower frequency arrives later
+    assert np.all(np.diff(tab[:, order], axis=1) <= 0)
+    # linear in DM / cadence up to rounding: halving the cadence doubles the delay (+-1)
+    tab2 = O.delay_table(freqs, dms, 0.5)
+    assert np.all(np.abs(tab2 - 2 * tab) <= 1)
+    # the rounding is well conditioned on the benchmark grids (ties far from FP64 error)
+    assert O.delay_fraction_margin(freqs, dms, 1.0) > 1e-6
+    assert O.delay_fraction_margin(freqs, np.arange(501) * 0.5, 1.0) > 1e-6
+
+
+def test_delay_textbook_magnitude():
+    """Lorimer & Kramer: ~4.15 ms * DM * nu_GHz^-2; DM 100 at 100 MHz vs infinity = 41.5 s."""
+    tab = O.delay_table([100.0, 1e9], [100.0], 1e-3)      # cadence 1 ms
+    assert abs(tab[0, 0] - 41488) <= 1
+    assert tab[0, 1] == 0
+
+
+# ----------------------------------------------------------------- a3 shift-sum
+def _frames_from_array(arr):
+    return lambda t: arr[t]
+
+
+def test_dm0_trial_is_plain_subband_sum():
+    rng = np.random.default_rng(0)
+    arr = rng.standard_normal((10, 5, 7, 9))
+    delays = np.zeros((1, 5), np.int64)
+    t0, D = O.dedisperse(_frames_from_array(arr), 6, delays, 0)
+    assert t0 == 6
+    np.testing.assert_allclose(D, arr[6].sum(axis=0), rtol=0, atol=1e-12)
+
+
+def test_shift_sum_impulse_lands_at_t0():
+    """A unit impulse at (f, t) reaches trial d exactly when t = t0 + delay[d][f]."""
+    F, T_len = 4, 12
+    delays = np.array([[0, 0, 0, 0], [3, 2, 1, 0], [5, 3, 1, 0], [4, 4, 0, 0]], np.int64)
+    for f in range(F):
+        for t in range(T_len):
+            arr = np.zeros((T_len, F, 3, 4))
+            arr[t, f, 1, 2] = 1.0
+            for d in range(delays.shape[0]):
+                dmax = int(delays[d].max())
+                for T in range(dmax, T_len):
+                    t0, D = O.dedisperse(_frames_from_array(arr), T, delays, d)
+                    expect = 1.0 if t == t0 + delays[d, f] else 0.0
+                    assert D[1, 2] == expect and D.sum() == expect
+
+
+def test_shift_sum_linearity():
+    rng = np.random.default_rng(1)
+    a = rng.standard_normal((8, 3, 5, 6))
+    b = rng.standard_normal((8, 3, 5, 6))
+    delays = np.array([[2, 1, 0]], np.int64)
+    _, Da = O.dedisperse(_frames_from_array(a), 5, delays, 0)
+    _, Db = O.dedisperse(_frames_from_array(b), 5, delays, 0)
+    _, Dab = O.dedisperse(_frames_from_array(2 * a - b), 5, delays, 0)
+    np.testing.assert_allclose(Dab, 2 * Da - Db, atol=1e-12)
+
+
+# ----------------------------------------------------------------- a4 / a5 box filter
+@pytest.mark.parametrize("r", [1, 2, 3])
+def test_box_filter_matches_brute_force(r):
+    rng = np.random.default_rng(2 + r)
+    img = rng.standard_normal((11, 17)) * 3 + np.arange(17)[None] * 0.5   # non-square, sloped
+    C = O.local_centre(img, r)
+    np.testing.assert_allclose(C, brute_box_mean(img, r), rtol=0, atol=1e-12)
+    S = O.local_spread(img, C, r)
+    np.testing.assert_allclose(S, brute_spread(img, brute_box_mean(img, r), r), rtol=0, atol=1e-12)
+
+
+def test_window_count_closed_form():
+    H, W, r = 9, 14, 3
+    n = O.window_count(H, W, r)
+    for y in range(H):
+        for x in range(W):
+            ny = min(y + r, H - 1) - max(y - r, 0) + 1
+            nx = min(x + r, W - 1) - max(x - r, 0) + 1
+            assert n[y, x] == ny * nx
+
+
+def test_constant_image_has_zero_spread():
+    img = np.full((20, 30), 7.25)
+    C = O.local_centre(img, 5)
+    S = O.local_spread(img, C, 5)
+    np.testing.assert_allclose(C, 7.25, atol=1e-12)
+    np.testing.assert_allclose(S, 0.0, atol=1e-20)
+    res = O.detect(img, 5, 1.0)
+    assert not res["mask"].any() and np.all(res["snr"] == 0)
+
+
+def test_snr_affine_invariance():
+    rng = np.random.default_rng(4)
+    img = rng.standard_normal((24, 21))
+    a = O.detect(img, 4, 2.0)
+    b = O.detect(3.5 * img - 11.0, 4, 2.0)
+    np.testing.assert_allclose(a["snr"], b["snr"], atol=1e-9)
+    assert np.array_equal(a["mask"], b["mask"])
+
+
+# ----------------------------------------------------------------- a6 detection
+def test_local_max_matches_brute_force():
+    rng = np.random.default_rng(5)
+    img = rng.integers(0, 4, (13, 10)).astype(float)     # many ties
+    assert np.array_equal(O.local_max_mask(img), brute_local_max(img))
+
+
+def test_plateau_ties_all_emitted():
+    img = np.zeros((9, 9))
+    img[4, 4] = img[4, 5] = 10.0
+    q = O.local_max_mask(img)
+    assert q[4, 4] and q[4, 5]
+    assert not q[3, 4]
+
+
+def test_iid_noise_local_max_fraction_is_one_ninth():
+    rng = np.random.default_rng(6)
+    img = rng.standard_normal((400, 400))
+    frac = O.local_max_mask(img)[1:-1, 1:-1].mean()
+    n = 398 * 398
+    sigma = math.sqrt((1 / 9) * (8 / 9) / n) * 3    # neighbouring maxima are dependent
+    assert abs(frac - 1 / 9) < 5 * sigma
+
+
+def test_threshold_is_strict():
+    rng = np.random.default_rng(7)
+    img = rng.standard_normal((31, 31))
+    img[15, 15] = 9.0
+    base = O.detect(img, 5, 0.0)
+    k = base["snr"][15, 15]
+    assert O.detect(img, 5, k)["mask"][15, 15] == False          # noqa: E712  (x > kappa)
+    assert O.detect(img, 5, np.nextafter(k, -np.inf))["mask"][15, 15]
+
+
+def test_noise_false_alarm_rate_follows_gaussian_tail():
+    """App. B.1: Pr(type-1 error) = 1 - Phi(kappa) for pure N(0, n^2) noise."""
+    rng = np.random.default_rng(8)
+    H = W = 64
+    frames = 600
+    counts = {3.5: 0, 4.0: 0}
+    delays = np.zeros((1, 16), np.int64)            # DM 0: independent frames
+    for t in range(frames):
+        cube = rng.standard_normal((16, H, W))
+        _, D = O.dedisperse(lambda _t, c=cube: c, 0, delays, 0)
+        snr = O.detect(D, 15, 99.0)["snr"]
+        for k in counts:
+            counts[k] += int((snr > k).sum())
+    for k, got in counts.items():
+        expect = H * W * frames * (1 - phi(k))
+        tol = 5 * math.sqrt(expect) + 0.10 * expect
+        assert abs(got - expect) < tol, (k, got, expect)
+
+
+def test_injected_pulse_recovered_at_pixel_and_dm():
+    """A dispersed pulse (paper's Sec. 3.2 model) is found at its pixel, in a trial whose
+    rounded delay row is that of the injected DM."""
+    spec = synth.spec_aartfaac(H=96, W=96, n_sources=0, gradient_amp=0.0, n_pulses=0,
+                               n_frames=80, dm_grid=np.arange(0, 161, dtype=np.float64))
+    pulse = synth.Pulse(y=40, x=57, t0=20.0, dm=100.0, width=1.0, alpha=0.0, amp=8.0)
+    st = synth.SyntheticStream(spec, seed=3, pulses=[pulse])
+    frame_at = lambda t: st.frame(t).astype(np.float64)
+    delays = O.delay_table(spec.freqs_mhz, spec.dm_grid, 1.0)
+    T = 20 + int(delays.max(axis=1)[100])
+    true_row = delays[100]
+    best = None
+    for d in range(len(spec.dm_grid)):
+        if int(delays[d].max()) != T - 20:
+            continue                      # only trials whose t0 is the pulse's
+        _, D = O.dedisperse(frame_at, T, delays, d)
+        res = O.detect(D, spec.box_r, spec.kappa)
+        if best is None or res["snr"][40, 57] > best[0]:
+            best = (res["snr"][40, 57], d, res["mask"][40, 57])
+    snr, d_best, det = best
+    assert det and snr > 15
+    assert np.array_equal(delays[d_best], true_row) or abs(d_best - 100) <= 1
+
+
+# ----------------------------------------------------------------- a7 stats
+def test_frame_stats_against_fsum():
+    rng = np.random.default_rng(9)
+    snr = rng.standard_normal((50, 40)) * 1e3 + 1e-3
+    valid = rng.random((50, 40)) > 0.2
+    mean, rms, n = O.frame_stats(snr, valid)
+    v = snr[valid].tolist()
+    assert n == len(v)
+    assert abs(mean - math.fsum(v) / n) <= 1e-12 * abs(math.fsum(v) / n) + 1e-15
+    assert abs(rms - math.sqrt(math.fsum(x * x for x in v) / n)) <= 1e-12 * rms
+
+
+# ----------------------------------------------------------------- a8 dynspec
+def test_dynspec_is_direct_indexing_of_frames():
+    spec = synth.spec_tiny()
+    st = synth.SyntheticStream(spec, seed=11)
+    T, Tw = 20, 6
+    cands = [(0, 0), (10, 63), (33, 17)]
+    out = O.dynspec(lambda t: st.frame(t), T, Tw, cands, 0)
+    for n, (y, x) in enumerate(cands):
+        for tau in range(Tw):
+            np.testing.assert_array_equal(out[n, :, tau], st.frame(T - Tw + 1 + tau)[:, y, x])
+    outb = O.dynspec(lambda t: st.frame(t), T, Tw, cands, 1)
+    fr = st.frame(T)
+    assert outb[1, 3, Tw - 1] == max(fr[3, yy, xx] for yy in (9, 10, 11) for xx in (62, 63))
+
+
+# ----------------------------------------------------------------- storage rounding
+def test_storage_round_ties_to_even():
+    x = np.array([1.0 + 2.0 ** -11, 1.0 + 3 * 2.0 ** -11, 65504.0, 1.0 + 2.0 ** -8])
+    h = O.storage_round(x, "fp16")
+    assert h[0] == 1.0 and h[1] == 1.0 + 2 * 2.0 ** -10 and h[2] == 65504.0
+    b = O.storage_round(x, "bf16")
+    assert b[3] == 1.0                     # 1 + 2^-8 is a tie in bf16 -> even (1.0)
+
+
+# ----------------------------------------------------------------- whole push
+def test_search_push_warmup_and_order():
+    spec = synth.spec_tiny()
+    st = synth.SyntheticStream(spec, seed=12)
+    delays = O.delay_table(spec.freqs_mhz, spec.dm_grid, spec.cadence_s)
+    dmax = delays.max(axis=1)
+    fa = lambda t: st.frame(t).astype(np.float64)
+    # at T = 0 only the trials without delay are active
+    cands, stats, _ = O.search_push(fa, 0, delays, spec.box_r, spec.kappa)
+    assert set(stats) == {d for d in range(spec.n_dm) if dmax[d] == 0}
+    cands, stats, _ = O.search_push(fa, 5, delays, spec.box_r, spec.kappa)
+    assert set(stats) == set(range(spec.n_dm))
+    keys = [(c[0], c[1], c[2], c[3]) for c in cands]
+    assert keys == sorted(keys) and len(set(keys)) == len(keys)
+    # the injected DM-7 pulse is detected at its pixel in the push that completes its sweep
+    p = st.pulses[0]
+    t0 = int(round(p.t0))
+    hits = []
+    for T in range(t0, t0 + int(dmax.max()) + 1):
+        cs, _, _ = O.search_push(fa, T, delays, spec.box_r, spec.kappa)
+        hits += [c for c in cs if (c[2], c[3]) == (p.y, p.x) and c[0] == t0]
+    assert hits and max(c[4] for c in hits) > 8
+
+
+@pytest.mark.parametrize("r", [2, 7])
+def test_lone_delta_snr_closed_form(r):
+    """Two-pass chain on a lone delta over a zero background: C = A/n on the window,
+    S(p) = A^2 (n-1)/n^2, hence snr(p) = sqrt(n - 1) for any amplitude A."""
+    size = 4 * r + 9
+    for A in (1.0, 37.5):
+        img = np.zeros((size, size))
+        c = size // 2
+        img[c, c] = A
+        res = O.detect(img, r, 0.0)
+        n = (2 * r + 1) ** 2
+        assert abs(res["snr"][c, c] - math.sqrt(n - 1)) < 1e-9
+        assert res["mask"][c, c] and res["mask"].sum() == 1
+
+
+# ----------------------------------------------------------------- planted mistakes
+def _pins_box(centre, spread):
+    rng = np.random.default_rng(21)
+    img = rng.standard_normal((9, 13)) + np.arange(13)[None] * 0.3
+    C = centre(img, 2)
+    ok = np.allclose(C, brute_box_mean(img, 2), atol=1e-12)
+    ok &= np.allclose(spread(img, C, 2), brute_spread(img, brute_box_mean(img, 2), 2), atol=1e-12)
+    return ok
+
+
+def test_pins_catch_planted_box_mistakes():
+    assert _pins_box(O.local_centre, O.local_spread)
+    full_norm = lambda D, r: O.box_sum(D, r) / (2 * r + 1) ** 2
+    assert not _pins_box(full_norm, O.local_spread)                      # no edge truncation
+    one_pass = lambda D, C, r: O.local_centre(D * D, r) - C * C
+    assert not _pins_box(O.local_centre, one_pass)                       # E[x^2]-E[x]^2
+    short = lambda D, r: O.window_sum_1d(O.window_sum_1d(D, r, 1), r - 1, 0) / O.window_count(*D.shape, r)
+    assert not _pins_box(short, O.local_spread)                          # wrong radius on one axis
+    centre_here = lambda D, C, r: O.box_sum(D * D, r) / O.window_count(*D.shape, r) - 2 * C * O.local_centre(D, r) + C * C
+    assert not _pins_box(O.local_centre, centre_here)
+
+
+def test_pins_catch_planted_shift_sign():
+    def wrong_dedisperse(frame_at, T, delays, d):
+        row = delays[d]
+        t0 = T - int(row.max())
+        D = 0
+        for f in range(len(row)):
+            D = D + frame_at(t0 + int(row.max() - row[f]))[f]      # reversed shift
+        return t0, D
+    delays = np.array([[3, 2, 1, 0]], np.int64)
+    arr = np.zeros((8, 4, 2, 2))
+    arr[6, 1, 0, 0] = 1.0                       # impulse at f=1, t=6 -> t0 = 4 at T = 7
+    _, D = wrong_dedisperse(_frames_from_array(arr), 7, delays, 0)
+    _, Dok = O.dedisperse(_frames_from_array(arr), 7, delays, 0)
+    assert Dok[0, 0] == 1.0 and D[0, 0] != 1.0
