@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Throughput of the image-plane dispersed-transient search on the AARTFAAC-shaped
+workload: 1024x1024 px, 16 subbands (two groups of 8 at 57.6 and 61.2 MHz),
+251 DM trials (0..250 step 1), ring depth 48, 31x31 background box, kappa 6.
+
+One step = one push of a new frame through the whole path (ingest, shift-sum,
+box centre / spread, S/N threshold + 3x3 local maximum, candidate ordering,
+per-trial stats).  Metric: pixel * DM-trials per second (H*W*N_DM per frame).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype fp32|fp16|bf16]
+  python bench.py --impl reference ...     # the FP64 CPU oracle on the same metric
+
+Under torchrun (N > 1) every rank runs an independent stream on its own GPU
+(weak scaling, no collective on the data path); rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "pixel*DM-trials/s"
+WORKLOAD = "aartfaac-1024x1024-16sb-251dm-depth48-box31"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pool", type=int, default=12, help="distinct synthetic frames cycled")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_spec(dtype):
+    return synth.spec_aartfaac(dtype=dtype)
+
+
+def algorithmic_bytes(spec, delays, n_distinct):
+    """Bytes a push must move at minimum, per stage, with storage type of b bytes."""
+    b = 4 if spec.dtype == "fp32" else 2
+    HW = spec.H * spec.W
+    lags = delays.max(axis=1)[:, None] - delays
+    U = sum(len(np.unique(lags[:, f])) for f in range(spec.F))
+    ring_reads = U * HW * b
+    return dict(
+        path=ring_reads + spec.F * HW * (4 + b),
+        ingest=spec.F * HW * (4 + b),
+        dedisperse=ring_reads + n_distinct * HW * 4,
+        filter_detect=n_distinct * HW * 4,
+        U=U,
+    )
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample(spec, frame_at, T, delays, dms):
+    from oracle import lpf_oracle as O
+    t = time.perf_counter()
+    O.search_push(frame_at, T, delays, spec.box_r, spec.kappa, dms=dms)
+    return time.perf_counter() - t
+
+
+def cpu_baseline(spec, st, delays, n_dm=12):
+    """The FP64 oracle (as it stands, one process) on a bounded sample of one push."""
+    import functools
+    fa = functools.lru_cache(maxsize=64)(lambda t: st.frame(t).astype(np.float64))
+    T = int(delays.max())
+    dms = [int(d) for d in np.linspace(0, spec.n_dm - 1, n_dm).round()]
+    fa_warm = [fa(T - k) for k in range(int(delays.max()) + 1)]  # generation outside the timing
+    del fa_warm
+    secs = oracle_sample(spec, fa, T, delays, dms)
+    val = spec.H * spec.W * len(dms) / secs
+    return {"value": val, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"one push (T={T}) of the {spec.H}x{spec.W} stream, {len(dms)} of "
+                      f"{spec.n_dm} DM trials, FP64 NumPy single process, {secs:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    spec = workload_spec(args.dtype)
+    from oracle import lpf_oracle as O
+    import functools
+    st = synth.SyntheticStream(spec, seed=1)
+    delays = O.delay_table(spec.freqs_mhz, spec.dm_grid, spec.cadence_s)
+    fa = functools.lru_cache(maxsize=128)(lambda t: O.storage_round(st.frame(t), spec.dtype))
+    T0 = int(delays.max())
+    per_step = 2    # DM trials per step: the oracle's bounded sample of one push
+    for w in range(args.warmup):
+        for k in range(int(delays.max()) + 1):
+            fa(T0 + w - k)
+    tot = 0.0
+    for k in range(args.steps):
+        T = T0 + (k % 4)
+        for j in range(int(delays.max()) + 1):
+            fa(T - j)
+        dms = [(k * per_step + j) % spec.n_dm for j in range(per_step)]
+        tot += oracle_sample(spec, fa, T, delays, dms)
+    val = spec.H * spec.W * per_step * args.steps / tot
+    sample = (f"each step: {per_step} of {spec.n_dm} DM trials of one push of the "
+              f"{spec.H}x{spec.W} stream, FP64 NumPy single process")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "storage": args.dtype,
+                                            "sample_dm_per_step": per_step},
+            "cpu_baseline": {"value": val, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_2103_15418_b300 as lpf
+    from oracle import lpf_oracle as O   # host delay table for the byte counts only
+
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = workload_spec(args.dtype)
+    st = synth.SyntheticStream(spec, seed=1 + rank)
+    pool = [torch.from_numpy(st.frame(t)) for t in range(args.pool)]
+    pool_dev = [p.to(dev) for p in pool]
+    pool_pin = [p.pin_memory() for p in pool]
+    cur = torch.cuda.current_stream(dev)
+    s = lpf.Stream(spec.H, spec.W, spec.freqs_mhz, spec.dm_grid, spec.depth, kappa=spec.kappa,
+                   box_r=spec.box_r, dtype=args.dtype, result_slots=3, cuda_stream=cur)
+    info = s.info()
+    delays = s.delay_table()
+    nbytes = algorithmic_bytes(spec, delays, info["n_distinct"])
+    depth = spec.depth
+    T = 0
+    polled = []
+
+    def push(T):
+        s.push(pool_dev[T % args.pool], T)
+
+    def poll():
+        _, c, n, _ = s.poll(timeout_ms=600000)
+        polled.append(n)
+
+    # fill the ring so every trial is active, then warm up
+    for _ in range(depth + args.warmup):
+        push(T)
+        T += 1
+        poll()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    s.kernel_times(reset=True)
+    s.set_profiling(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(cur)
+    push(T)
+    T += 1
+    for k in range(1, args.steps):
+        push(T)
+        T += 1
+        poll()
+    ev1.record(cur)
+    poll()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    s.set_profiling(False)
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    ktimes = s.kernel_times(reset=True)
+    if dist is not None:
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    ncand = float(np.mean(polled[-args.steps:]))
+    pix_dm = spec.H * spec.W * spec.n_dm
+    value = pix_dm * args.steps * ws / elapsed
+
+    # end to end through the C ABI with host buffers: H2D of the frame, D2H of the candidates
+    lat = []
+    e2e_cands = []
+    torch.cuda.synchronize()
+    t_e0 = time.perf_counter()
+    for k in range(args.e2e_steps):
+        t0 = time.perf_counter()
+        s.push_host(pool_pin[T % args.pool], T)
+        T += 1
+        _, c, n, _ = s.poll(timeout_ms=600000)
+        e2e_cands.append(n)
+        lat.append(time.perf_counter() - t0)
+    e2e_s = time.perf_counter() - t_e0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = pix_dm * args.e2e_steps * ws / e2e_s
+    s.close()
+
+    if rank != 0:
+        return
+    # dominant kernel and its roofline
+    names = list(ktimes)
+    dom = max(names, key=lambda n: ktimes[n][0])
+    dom_ms = ktimes[dom][0] / max(ktimes[dom][1], 1)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    alg = nbytes.get(dom)
+    roof = None
+    if alg is not None:
+        ach = alg / (dom_ms / 1e3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": None, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": alg, "avg_launch_ms": dom_ms}
+    path_ach = nbytes["path"] / (elapsed / args.steps) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded AARTFAAC-shaped stream: noise, 3-sigma cosine gradient, "
+                "500 Gaussian-PSF sources, 20 dispersed pulses)",
+        "config": {"workload": WORKLOAD, "H": spec.H, "W": spec.W, "subbands": spec.F,
+                   "dm_trials": spec.n_dm, "depth": depth, "box": 2 * spec.box_r + 1,
+                   "storage": args.dtype, "distinct_delay_rows": info["n_distinct"],
+                   "l2": "inputs larger than L2 (ring %.2f GB)" % (info["ring_bytes"] / 1e9),
+                   "parallelism": f"{ws} independent stream(s), one per GPU"},
+        "e2e": {"value": e2e_value, "unit": METRIC,
+                "h2d_bytes_per_step": spec.F * spec.H * spec.W * 4,
+                "d2h_bytes_per_step": int(np.mean(e2e_cands) * 24 + spec.n_dm * 16)},
+        "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
+                       "p99": 1e3 * float(np.percentile(lat, 99)), "what": "push_frame_host -> poll"},
+        # per push: ingest, counter reset, shift-sum, filter, 3 per sort pass, format, stats
+        "gpu_launches": int(args.steps * (6 + 3 * _passes(spec))),
+        "roofline": roof,
+        "path_roofline": {"bound": "hbm", "achieved": path_ach, "peak": hbm_peak, "unit": "GB/s",
+                          "frac": path_ach / hbm_peak,
+                          "algorithmic_bytes_per_step": nbytes["path"],
+                          "note": "sum over subbands of distinct delay planes read once + ingest"},
+        "kernel_ms_per_step": {n: ktimes[n][0] / max(ktimes[n][1], 1) for n in names},
+        "candidates_per_step": ncand,
+        "clocks": clk,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(spec, st, delays)
+    print(json.dumps(line), flush=True)
+
+
+def _passes(spec):
+    bits = lambda v: max(1, int(np.ceil(np.log2(v))))
+    return (bits(spec.W) + bits(spec.H) + bits(spec.n_dm) + 7) // 8
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

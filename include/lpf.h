@@ -1,0 +1,190 @@
+/*
+ * lpf.h -- C ABI of the B300 image-plane dispersed-transient search.
+ *
+ * Method: Ruhe et al., "Detecting Dispersed Radio Transients in Real Time Using
+ * Convolutional Neural Networks" (arXiv 2103.15418).  The library runs, per new
+ * frame of F subband images, the brute-force image-plane dedispersion search:
+ *
+ *   delay table   delay[d][f] = floor(C_DM * DM_d * (nu_f^-2 - nu_ref^-2) / cadence + 1/2)
+ *                 with C_DM = 4.148808e3 s MHz^2 cm^3/pc and nu_ref = max_f nu_f
+ *                 (Sec. 3.2, dispersion-delay equation);
+ *   shift-sum     D_d = sum_f X_f(t0 + delay[d][f]), t0 = T - max_f delay[d][f]
+ *                 (App. B.2, "perfect dedispersion" before averaging);
+ *   local centre  C = box mean of D over the (2r+1)^2 window clipped to the image
+ *                 (Sec. 2.1.1, C := G * X with the uniform kernel, normalised);
+ *   local spread  S = box mean of (D - C)^2, the square taken per pixel first
+ *                 (Sec. 2.1.1, S := G * (X - C)^2);
+ *   detection     snr = (D - C)/sqrt(S); candidate iff snr > kappa, S > 0 and D is
+ *                 the maximum of its 3x3 window clipped to the image, ties included
+ *                 (Sec. 2.1.1 threshold y, Sec. 2.1.2 max filter q and p = q AND y);
+ *   statistics    per DM trial, mean and RMS of snr over pixels with S > 0;
+ *   dynspec       per candidate, the F x Tw fluxes of the Tw most recent frames at its
+ *                 pixel, optionally the box maximum (Sec. 2.2 flux measurement and
+ *                 backward fill), the input of the paper's CNN (Sec. 2.3).
+ *
+ * All compute runs in CUDA kernels for sm_103a; there is no CPU fallback.  A call
+ * that needs the GPU fails with LPF_E_CUDA when no usable device is present.
+ *
+ * Threading: one host thread per stream handle at a time.  Handles are
+ * independent; different handles may be driven from different threads.
+ * Errors: every call returns LPF_OK (0) or a negative LPF_E_* code; nothing
+ * aborts or throws across the ABI.  lpf_strerror() names a code.
+ */
+#ifndef LPF_H
+#define LPF_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes */
+#define LPF_OK            0
+#define LPF_E_ARG        -1   /* invalid argument (null pointer, size out of range, ...) */
+#define LPF_E_DEPTH      -2   /* buffer_depth < max delay + 1, or Tw > buffer_depth     */
+#define LPF_E_ORDER      -3   /* pushed frame index is not the previous one + 1          */
+#define LPF_E_OOM        -4   /* device or pinned-host allocation failed                 */
+#define LPF_E_BUDGET     -5   /* server: stream does not fit the HBM budget at all       */
+#define LPF_E_TRUNCATED  -6   /* more candidates than the output (or cand_cap) can hold  */
+#define LPF_E_STALE      -7   /* frames needed by extract_dynspec left the ring buffer   */
+#define LPF_E_TIMEOUT    -8   /* poll: the frame's work did not finish within timeout_ms */
+#define LPF_E_CUDA       -9   /* a CUDA runtime call failed (no device, launch failure)  */
+#define LPF_E_BUSY      -10   /* all result slots hold unpolled frames; poll first       */
+#define LPF_E_NODATA    -11   /* poll with no pushed-and-unpolled frame                  */
+
+/* storage type of the ring buffer (arithmetic is always FP32) */
+#define LPF_FP32 0
+#define LPF_FP16 1
+#define LPF_BF16 2
+
+typedef struct lpf_stream lpf_stream;   /* opaque; owns ring buffer, tables, scratch */
+
+typedef struct {
+    double cadence_s;     /* frame cadence in seconds (> 0)                     default 1.0   */
+    float  kappa;         /* S/N threshold (strict >)                            default 6.0   */
+    int    box_r;         /* background box radius r, window (2r+1)^2, 1..16      default 15    */
+    int    lmax_r;        /* local-maximum radius; only 1 (3x3) is supported      default 1     */
+    int    dtype;         /* LPF_FP32 / LPF_FP16 / LPF_BF16 ring storage          default FP32  */
+    int    cand_cap;      /* device candidate capacity per frame (records)       default 1<<20 */
+    int    dyn_box_r;     /* dynspec box radius (0 = the candidate pixel)         default 0     */
+    int    result_slots;  /* frames that may be pushed but not yet polled, 1..16  default 2     */
+    void*  cuda_stream;   /* cudaStream_t to run on; NULL = a private non-blocking stream    */
+} lpf_params;
+
+/* One candidate: pixel (y, x) of DM trial dm_idx (index into dm_grid) whose
+ * dispersed sweep arrives at nu_ref in frame t0 (so it is completed by frame
+ * t0 + max_f delay[dm_idx][f]), with its S/N.  24 bytes, no padding. */
+typedef struct {
+    int64_t t0;
+    int32_t dm_idx;
+    int32_t y;
+    int32_t x;
+    float   snr;
+} lpf_candidate;
+
+typedef struct {
+    int     H, W, F, n_dm, depth, dtype;
+    int     n_distinct;       /* DM trials with distinct delay rows (computed once each) */
+    int     max_delay;        /* max over trials of max_f delay[d][f], frames           */
+    size_t  ring_bytes;       /* device bytes of the ring buffer                         */
+    size_t  device_bytes;     /* all device bytes owned by the stream                    */
+    int64_t frames_pushed;
+    int64_t last_T;
+} lpf_stream_info_t;
+
+/* Fill *p with the defaults listed above. */
+void lpf_default_params(lpf_params* p);
+
+/*
+ * Open a stream: H x W images, F subbands with centre frequencies freqs_mhz[F]
+ * (MHz, > 0, host), n_dm trial DMs dm_grid[n_dm] (pc cm^-3, >= 0, host), ring
+ * of buffer_depth frames.  params may be NULL (defaults).  The library copies
+ * every input; the caller keeps nothing alive.  Builds the delay table in FP64
+ * on the host (Sec. 3.2) and allocates the ring buffer and scratch on the
+ * current CUDA device.
+ * Errors: LPF_E_ARG (sizes <= 0, box_r outside 1..16, lmax_r != 1, bad dtype,
+ * non-positive frequency or cadence, negative DM), LPF_E_DEPTH (buffer_depth <
+ * max delay + 1), LPF_E_OOM, LPF_E_CUDA (no device).
+ */
+int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_mhz,
+                    int n_dm, const double* dm_grid, int buffer_depth, const lpf_params* params);
+
+/*
+ * Push frame T: frame_dev is a DEVICE pointer to F*H*W FP32 values laid out
+ * [F][H][W] (row-major, subband-major), on the stream's device.  The work is
+ * enqueued on the stream's CUDA stream and the call returns at once; the
+ * caller keeps frame_dev unchanged until the stream has consumed it (after
+ * lpf_poll_candidates returns for T, or lpf_stream_sync).  The first push may
+ * use any T >= 0; later pushes must use the previous T + 1.  Push T produces
+ * the candidates of every DM trial d with T - max_f delay[d][f] >= first T.
+ * Errors: LPF_E_ARG, LPF_E_ORDER, LPF_E_BUSY (result_slots frames unpolled), LPF_E_CUDA.
+ */
+int lpf_push_frame(lpf_stream* s, const float* frame_dev, int64_t T);
+
+/* Same as lpf_push_frame with a HOST frame (pinned or pageable), copied to the
+ * device inside the call's stream order; the host buffer may be reused when the
+ * call returns if it is pageable, after the next poll if it is pinned. */
+int lpf_push_frame_host(lpf_stream* s, const float* frame_host, int64_t T);
+
+/*
+ * Poll the oldest pushed-and-unpolled frame.  Waits up to timeout_ms (< 0:
+ * forever) for its work, then copies its candidates into out_host[cap] (HOST),
+ * sorted by (t0, dm_idx, y, x), and sets *n_out to the total number found and
+ * *T_out to the frame index.  Returns LPF_E_TRUNCATED (with out_host holding
+ * the first min(cap, cand_cap) records of the found set, sorted; which records
+ * were dropped beyond cand_cap is unspecified) when *n_out > cap or the device
+ * capacity cand_cap overflowed; LPF_E_TIMEOUT (frame stays queued) or
+ * LPF_E_NODATA otherwise.  out_host may be NULL when cap == 0.
+ */
+int lpf_poll_candidates(lpf_stream* s, lpf_candidate* out_host, int cap, int* n_out,
+                        int64_t* T_out, int timeout_ms);
+
+/*
+ * Gather the dynamic spectra of n candidates c_host[n] (HOST; only y and x are
+ * read) for the most recently polled frame T: out_dev (DEVICE, FP32,
+ * [n][F][Tw]) receives out[i][f][tau] = X_f(T - Tw + 1 + tau) at (y_i, x_i), or
+ * the maximum over the (2 dyn_box_r + 1)^2 box clipped to the image.  Enqueued
+ * on the stream; out_dev is valid once the stream reaches it (lpf_stream_sync).
+ * Errors: LPF_E_ARG (pixel outside the image, n < 0, Tw < 1), LPF_E_DEPTH (Tw >
+ * buffer_depth), LPF_E_STALE (a needed frame was overwritten or precedes the
+ * first push), LPF_E_NODATA (nothing polled yet).
+ */
+int lpf_extract_dynspec(lpf_stream* s, const lpf_candidate* c_host, int n, int Tw,
+                        float* out_dev);
+
+/* Copy the integer delay table [n_dm][F] (frames) into out (HOST). */
+int lpf_get_delay_table(const lpf_stream* s, int32_t* out);
+
+/* Copy [n_dm][2] = (mean, rms) of snr over pixels with S > 0 of every DM trial
+ * of the most recently polled frame into out (HOST, FP64); NaN for trials not
+ * active at that frame.  Partial sums are FP32 over at most 33 pixels per
+ * thread and FP64 above that. */
+int lpf_get_stats(const lpf_stream* s, double* out);
+
+int lpf_stream_info(const lpf_stream* s, lpf_stream_info_t* out);
+
+/* Wait (without limit) for all work enqueued on the stream. */
+int lpf_stream_sync(lpf_stream* s);
+
+/* Release every resource of the stream after waiting for its work. NULL is OK. */
+int lpf_stream_close(lpf_stream* s);
+
+const char* lpf_strerror(int code);
+
+/*
+ * Profiling: when on, every push records CUDA events around each kernel stage
+ * on the stream it runs on.  lpf_get_kernel_times fills up to n entries of
+ * names[] (static strings), total_ms[] and launches[] accumulated since the
+ * last reset (reset != 0 clears them after reading) and returns the number of
+ * stages.  Reading synchronises the stream.
+ */
+int lpf_set_profiling(lpf_stream* s, int on);
+int lpf_get_kernel_times(lpf_stream* s, const char** names, double* total_ms,
+                         int64_t* launches, int n, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LPF_H */

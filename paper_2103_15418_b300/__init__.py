@@ -1,0 +1,226 @@
+"""Python binding of liblpf, the B300 image-plane dispersed-transient search.
+
+Argument marshalling only: every step of the search runs in the CUDA kernels of
+liblpf.so (built in-tree by build.py for sm_103a).  PyTorch is used for device
+memory and CUDA streams.  There is no CPU fallback: if the library cannot be
+loaded, or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import (POINTER, Structure, c_char_p, c_double, c_float, c_int, c_int32, c_int64,
+                    c_size_t, c_void_p)
+from typing import Dict, Optional, Tuple
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblpf.so")
+
+LPF_OK = 0
+LPF_E_ARG, LPF_E_DEPTH, LPF_E_ORDER, LPF_E_OOM, LPF_E_BUDGET = -1, -2, -3, -4, -5
+LPF_E_TRUNCATED, LPF_E_STALE, LPF_E_TIMEOUT, LPF_E_CUDA = -6, -7, -8, -9
+LPF_E_BUSY, LPF_E_NODATA = -10, -11
+DTYPES = {"fp32": 0, "fp16": 1, "bf16": 2}
+
+# Every exported symbol declared in include/lpf.h (checked by the CPU tests).
+EXPORTS = [
+    "lpf_default_params", "lpf_stream_open", "lpf_push_frame", "lpf_push_frame_host",
+    "lpf_poll_candidates", "lpf_extract_dynspec", "lpf_get_delay_table", "lpf_get_stats",
+    "lpf_stream_info", "lpf_stream_sync", "lpf_stream_close", "lpf_strerror",
+    "lpf_set_profiling", "lpf_get_kernel_times",
+]
+
+
+class Params(Structure):
+    _fields_ = [("cadence_s", c_double), ("kappa", c_float), ("box_r", c_int), ("lmax_r", c_int),
+                ("dtype", c_int), ("cand_cap", c_int), ("dyn_box_r", c_int),
+                ("result_slots", c_int), ("cuda_stream", c_void_p)]
+
+
+class Candidate(Structure):
+    _fields_ = [("t0", c_int64), ("dm_idx", c_int32), ("y", c_int32), ("x", c_int32),
+                ("snr", c_float)]
+
+
+class StreamInfo(Structure):
+    _fields_ = [("H", c_int), ("W", c_int), ("F", c_int), ("n_dm", c_int), ("depth", c_int),
+                ("dtype", c_int), ("n_distinct", c_int), ("max_delay", c_int),
+                ("ring_bytes", c_size_t), ("device_bytes", c_size_t),
+                ("frames_pushed", c_int64), ("last_T", c_int64)]
+
+
+CANDIDATE_DTYPE = np.dtype([("t0", "<i8"), ("dm_idx", "<i4"), ("y", "<i4"), ("x", "<i4"),
+                            ("snr", "<f4")])
+assert CANDIDATE_DTYPE.itemsize == ctypes.sizeof(Candidate) == 24
+
+_lib = None
+
+
+class LpfError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = _lib.lpf_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+
+
+def load(path: Optional[str] = None):
+    """Load liblpf.so (building it first if it is missing) and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        from . import build as _build
+        _build.build()
+    lib = ctypes.CDLL(path)
+    lib.lpf_default_params.argtypes = [POINTER(Params)]
+    lib.lpf_default_params.restype = None
+    lib.lpf_stream_open.argtypes = [POINTER(c_void_p), c_int, c_int, c_int, POINTER(c_double), c_int,
+                                    POINTER(c_double), c_int, POINTER(Params)]
+    lib.lpf_push_frame.argtypes = [c_void_p, c_void_p, c_int64]
+    lib.lpf_push_frame_host.argtypes = [c_void_p, c_void_p, c_int64]
+    lib.lpf_poll_candidates.argtypes = [c_void_p, c_void_p, c_int, POINTER(c_int), POINTER(c_int64), c_int]
+    lib.lpf_extract_dynspec.argtypes = [c_void_p, c_void_p, c_int, c_int, c_void_p]
+    lib.lpf_get_delay_table.argtypes = [c_void_p, c_void_p]
+    lib.lpf_get_stats.argtypes = [c_void_p, c_void_p]
+    lib.lpf_stream_info.argtypes = [c_void_p, POINTER(StreamInfo)]
+    lib.lpf_stream_sync.argtypes = [c_void_p]
+    lib.lpf_stream_close.argtypes = [c_void_p]
+    lib.lpf_strerror.argtypes = [c_int]
+    lib.lpf_strerror.restype = c_char_p
+    lib.lpf_set_profiling.argtypes = [c_void_p, c_int]
+    lib.lpf_get_kernel_times.argtypes = [c_void_p, POINTER(c_char_p), POINTER(c_double),
+                                         POINTER(c_int64), c_int, c_int]
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, what: str):
+    if rc != LPF_OK:
+        raise LpfError(rc, what)
+
+
+def default_params() -> Params:
+    p = Params()
+    load().lpf_default_params(ctypes.byref(p))
+    return p
+
+
+class Stream:
+    """One image stream: ring buffer, delay table and search state on one GPU."""
+
+    def __init__(self, H: int, W: int, freqs_mhz, dm_grid, depth: int, *, cadence_s: float = 1.0,
+                 kappa: float = 6.0, box_r: int = 15, dtype: str = "fp32", cand_cap: int = 1 << 20,
+                 dyn_box_r: int = 0, result_slots: int = 2, cuda_stream=None):
+        lib = load()
+        self.H, self.W = int(H), int(W)
+        self.freqs = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
+        self.dms = np.ascontiguousarray(dm_grid, dtype=np.float64)
+        self.F, self.n_dm, self.depth = len(self.freqs), len(self.dms), int(depth)
+        p = default_params()
+        p.cadence_s, p.kappa, p.box_r = cadence_s, kappa, box_r
+        p.dtype, p.cand_cap, p.dyn_box_r, p.result_slots = DTYPES[dtype], cand_cap, dyn_box_r, result_slots
+        if cuda_stream is not None:
+            p.cuda_stream = int(getattr(cuda_stream, "cuda_stream", cuda_stream))
+        self.params = p
+        self._cap = int(cand_cap)
+        h = c_void_p()
+        _check(lib.lpf_stream_open(ctypes.byref(h), self.H, self.W, self.F,
+                                   self.freqs.ctypes.data_as(POINTER(c_double)), self.n_dm,
+                                   self.dms.ctypes.data_as(POINTER(c_double)), self.depth,
+                                   ctypes.byref(p)), "lpf_stream_open")
+        self._h = h
+        self._out = np.zeros(self._cap, dtype=CANDIDATE_DTYPE)
+
+    # ---------------------------------------------------------------- pushes
+    def push(self, frame, T: int) -> None:
+        """frame: CUDA float32 tensor [F, H, W], contiguous, on this stream's device."""
+        if not (frame.is_cuda and frame.dtype.__str__() == "torch.float32" and frame.is_contiguous()):
+            raise ValueError("frame must be a contiguous float32 CUDA tensor")
+        if tuple(frame.shape) != (self.F, self.H, self.W):
+            raise ValueError(f"frame shape {tuple(frame.shape)} != {(self.F, self.H, self.W)}")
+        _check(load().lpf_push_frame(self._h, c_void_p(frame.data_ptr()), int(T)), "lpf_push_frame")
+
+    def push_host(self, frame, T: int) -> None:
+        """frame: host float32 array/tensor [F, H, W] (pinned for asynchronous copies)."""
+        ptr = frame.data_ptr() if hasattr(frame, "data_ptr") else frame.ctypes.data
+        n = frame.numel() if hasattr(frame, "numel") else frame.size
+        if n != self.F * self.H * self.W:
+            raise ValueError("frame size mismatch")
+        _check(load().lpf_push_frame_host(self._h, c_void_p(ptr), int(T)), "lpf_push_frame_host")
+
+    def poll(self, cap: Optional[int] = None, timeout_ms: int = -1):
+        """Candidates of the oldest unpolled frame: (T, records, n_found, truncated)."""
+        cap = self._cap if cap is None else int(cap)
+        buf = self._out if cap <= self._out.size else np.zeros(cap, dtype=CANDIDATE_DTYPE)
+        n = c_int(0)
+        T = c_int64(-1)
+        rc = load().lpf_poll_candidates(self._h, c_void_p(buf.ctypes.data), cap, ctypes.byref(n),
+                                        ctypes.byref(T), int(timeout_ms))
+        if rc not in (LPF_OK, LPF_E_TRUNCATED):
+            raise LpfError(rc, "lpf_poll_candidates")
+        k = min(n.value, cap, self._cap)
+        return T.value, buf[:k].copy(), n.value, rc == LPF_E_TRUNCATED
+
+    def dynspec(self, cands, Tw: int, out=None):
+        """FP32 CUDA tensor [n, F, Tw] of the candidates' dynamic spectra (last polled frame)."""
+        import torch
+        c = np.ascontiguousarray(cands, dtype=CANDIDATE_DTYPE)
+        n = len(c)
+        if out is None:
+            out = torch.empty((n, self.F, Tw), dtype=torch.float32, device="cuda")
+        _check(load().lpf_extract_dynspec(self._h, c_void_p(c.ctypes.data) if n else None, n, int(Tw),
+                                          c_void_p(out.data_ptr()) if n else None),
+               "lpf_extract_dynspec")
+        return out
+
+    # ---------------------------------------------------------------- queries
+    def delay_table(self) -> np.ndarray:
+        out = np.zeros((self.n_dm, self.F), dtype=np.int32)
+        _check(load().lpf_get_delay_table(self._h, c_void_p(out.ctypes.data)), "lpf_get_delay_table")
+        return out
+
+    def stats(self) -> np.ndarray:
+        out = np.zeros((self.n_dm, 2), dtype=np.float64)
+        _check(load().lpf_get_stats(self._h, c_void_p(out.ctypes.data)), "lpf_get_stats")
+        return out
+
+    def info(self) -> Dict[str, int]:
+        i = StreamInfo()
+        _check(load().lpf_stream_info(self._h, ctypes.byref(i)), "lpf_stream_info")
+        return {k: getattr(i, k) for k, _ in StreamInfo._fields_}
+
+    def sync(self) -> None:
+        _check(load().lpf_stream_sync(self._h), "lpf_stream_sync")
+
+    def set_profiling(self, on: bool) -> None:
+        _check(load().lpf_set_profiling(self._h, 1 if on else 0), "lpf_set_profiling")
+
+    def kernel_times(self, reset: bool = False) -> Dict[str, Tuple[float, int]]:
+        n = 16
+        names = (c_char_p * n)()
+        ms = (c_double * n)()
+        cnt = (c_int64 * n)()
+        k = load().lpf_get_kernel_times(self._h, names, ms, cnt, n, 1 if reset else 0)
+        if k < 0:
+            raise LpfError(k, "lpf_get_kernel_times")
+        return {names[i].decode(): (ms[i], cnt[i]) for i in range(k)}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().lpf_stream_close(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,691 @@
+// Host runtime and C ABI of the dispersed-transient search (see include/lpf.h).
+//
+// One lpf_stream owns: the FP64-built integer delay table and its distinct-row
+// plan, the device ring buffer, the dedispersed-image scratch, the candidate
+// sort buffers and a small ring of result slots (pushed-but-unpolled frames).
+// Every push enqueues, on the stream's CUDA stream:
+//   ingest -> shift-sum -> filter/detect -> radix sort -> format -> stats
+// and records an event; poll waits on that event with a deadline.
+#include "../../include/lpf.h"
+#include "lpf_kernels.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+namespace {
+
+constexpr double kCdmSeconds = 4.148808e3;   // s MHz^2 cm^3 / pc (Sec. 3.2)
+constexpr int kSortBlocks = 148;
+constexpr int kMaxSlots = 16;
+
+enum Stage { ST_INGEST, ST_DEDISP, ST_FILTER, ST_SORT, ST_FORMAT, ST_STATS, ST_N };
+const char* kStageNames[ST_N] = {"ingest", "dedisperse", "filter_detect", "sort", "format", "stats"};
+
+int ceil_log2(int64_t v) {
+    int b = 0;
+    while ((int64_t(1) << b) < v) ++b;
+    return b;
+}
+
+struct Slot {
+    int64_t T = -1;
+    int n_active = 0;
+    lpf::CandidateRec* d_out = nullptr;
+    double* d_stats = nullptr;     // [n_distinct][3]
+    cudaEvent_t done = nullptr;
+};
+
+}  // namespace
+
+struct lpf_stream {
+    int dev = 0;
+    int H = 0, W = 0, F = 0, n_dm = 0, depth = 0;
+    lpf_params prm{};
+    int64_t HW = 0, P = 0;
+    size_t elem = 4;
+
+    std::vector<int32_t> delay;      // [n_dm][F]
+    std::vector<int> dmax;           // per trial
+    int max_delay = 0;
+    // distinct delay rows, sorted by (max delay, first trial)
+    int n_distinct = 0;
+    std::vector<int> row_dmax;       // per distinct row
+    std::vector<int> row_of_d;
+    std::vector<int> member_start;   // [n_distinct + 1]
+    std::vector<int> member_ord;     // canonical rank of each member
+    std::vector<int> ord2d;          // canonical rank -> trial
+    int bx = 0, by = 0, bo = 0, key_bits = 0;
+
+    // device memory
+    void* ring = nullptr;
+    float* D = nullptr;
+    float* stage = nullptr;          // host-push staging frame
+    int16_t* d_lag = nullptr;
+    int* d_member_start = nullptr;
+    int* d_member_ord = nullptr;
+    int* d_ord2d = nullptr;
+    int* d_dmax = nullptr;
+    uint64_t* keys[2] = {nullptr, nullptr};
+    float* vals[2] = {nullptr, nullptr};
+    unsigned* d_counter = nullptr;
+    unsigned* d_hist = nullptr;
+    double* d_partials = nullptr;
+    int2* d_yx = nullptr;
+    int yx_cap = 0;
+    size_t device_bytes = 0;
+
+    // host pinned
+    unsigned* h_count = nullptr;     // [slots]
+    double* h_stats = nullptr;       // [slots][n_distinct][3]
+
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    cudaStream_t copy_st = nullptr;
+    Slot slots[kMaxSlots];
+    int n_slots = 2;
+    std::deque<int> pending;         // slot indices in push order
+    int next_slot = 0;
+
+    bool any_push = false;
+    int64_t T_first = 0, last_T = -1, frames_pushed = 0;
+    bool polled = false;
+    int64_t polled_T = -1;
+    int polled_slot = -1;
+    std::vector<double> last_stats; // [n_dm][2]
+
+    int tiles_x = 0, tiles_y = 0;
+    size_t filter_smem = 0;
+    int filter_rmax = 16;
+
+    bool profiling = false;
+    cudaEvent_t ev[kMaxSlots][ST_N + 1] = {};
+    bool prof_slot[kMaxSlots] = {};
+    double prof_ms[ST_N] = {};
+    int64_t prof_n[ST_N] = {};
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) {
+    return e == cudaSuccess ? LPF_OK : LPF_E_CUDA;
+}
+
+#define LPF_TRY(expr)                                   \
+    do {                                                \
+        cudaError_t _e = (expr);                        \
+        if (_e != cudaSuccess) return LPF_E_CUDA;       \
+    } while (0)
+
+template <typename T>
+int dev_alloc(lpf_stream* s, T** p, size_t count) {
+    size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return LPF_E_OOM;
+    }
+    s->device_bytes += bytes;
+    return LPF_OK;
+}
+
+void free_all(lpf_stream* s) {
+    if (!s) return;
+    cudaSetDevice(s->dev);
+    if (s->st) cudaStreamSynchronize(s->st);
+    void* ptrs[] = {s->ring, s->D, s->stage, s->d_lag, s->d_member_start, s->d_member_ord,
+                    s->d_ord2d, s->d_dmax, s->keys[0], s->keys[1], s->vals[0], s->vals[1],
+                    s->d_counter, s->d_hist, s->d_partials, s->d_yx};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (int i = 0; i < kMaxSlots; ++i) {
+        if (s->slots[i].d_out) cudaFree(s->slots[i].d_out);
+        if (s->slots[i].d_stats) cudaFree(s->slots[i].d_stats);
+        if (s->slots[i].done) cudaEventDestroy(s->slots[i].done);
+    }
+    for (auto& row : s->ev)
+        for (auto& e : row)
+            if (e) cudaEventDestroy(e);
+    if (s->h_count) cudaFreeHost(s->h_count);
+    if (s->h_stats) cudaFreeHost(s->h_stats);
+    if (s->copy_st) cudaStreamDestroy(s->copy_st);
+    if (s->own_stream && s->st) cudaStreamDestroy(s->st);
+}
+
+// Sec. 3.2 delay law, FP64 on the host: floor(C_DM DM (nu^-2 - nu_ref^-2) / cadence + 1/2).
+void build_delay_table(lpf_stream* s, const double* freqs, const double* dms) {
+    double ref = freqs[0];
+    for (int f = 1; f < s->F; ++f) ref = std::max(ref, freqs[f]);
+    s->delay.assign((size_t)s->n_dm * s->F, 0);
+    s->dmax.assign(s->n_dm, 0);
+    for (int d = 0; d < s->n_dm; ++d) {
+        int mx = 0;
+        for (int f = 0; f < s->F; ++f) {
+            double seconds = kCdmSeconds * dms[d] * (std::pow(freqs[f], -2.0) - std::pow(ref, -2.0));
+            int v = (int)std::floor(seconds / s->prm.cadence_s + 0.5);
+            s->delay[(size_t)d * s->F + f] = v;
+            mx = std::max(mx, v);
+        }
+        s->dmax[d] = mx;
+    }
+    s->max_delay = *std::max_element(s->dmax.begin(), s->dmax.end());
+}
+
+// Group trials with identical delay rows; order rows by (max delay, first trial);
+// canonical trial order is (t0 ascending = max delay descending, trial index).
+void build_plan(lpf_stream* s) {
+    std::map<std::vector<int32_t>, int> ids;
+    std::vector<std::vector<int>> groups;
+    std::vector<int> first_row_of_group;
+    for (int d = 0; d < s->n_dm; ++d) {
+        std::vector<int32_t> row(s->delay.begin() + (size_t)d * s->F, s->delay.begin() + (size_t)(d + 1) * s->F);
+        auto it = ids.find(row);
+        if (it == ids.end()) {
+            ids.emplace(row, (int)groups.size());
+            groups.push_back({d});
+        } else {
+            groups[it->second].push_back(d);
+        }
+    }
+    std::vector<int> order(groups.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        int da = s->dmax[groups[a][0]], db = s->dmax[groups[b][0]];
+        if (da != db) return da < db;
+        return groups[a][0] < groups[b][0];
+    });
+    s->n_distinct = (int)groups.size();
+    // canonical trial ranks
+    std::vector<int> tr(s->n_dm);
+    for (int d = 0; d < s->n_dm; ++d) tr[d] = d;
+    std::stable_sort(tr.begin(), tr.end(), [&](int a, int b) {
+        if (s->dmax[a] != s->dmax[b]) return s->dmax[a] > s->dmax[b];
+        return a < b;
+    });
+    s->ord2d = tr;
+    std::vector<int> ord_of_d(s->n_dm);
+    for (int i = 0; i < s->n_dm; ++i) ord_of_d[tr[i]] = i;
+    s->row_of_d.assign(s->n_dm, 0);
+    s->row_dmax.clear();
+    s->member_start.assign(1, 0);
+    s->member_ord.clear();
+    for (int rr = 0; rr < s->n_distinct; ++rr) {
+        const auto& g = groups[order[rr]];
+        s->row_dmax.push_back(s->dmax[g[0]]);
+        for (int d : g) {
+            s->row_of_d[d] = rr;
+            s->member_ord.push_back(ord_of_d[d]);
+        }
+        s->member_start.push_back((int)s->member_ord.size());
+    }
+}
+
+int n_active_rows(const lpf_stream* s, int64_t T) {
+    int64_t span = T - s->T_first;
+    int n = 0;
+    while (n < s->n_distinct && s->row_dmax[n] <= span) ++n;
+    return n;
+}
+
+template <typename TS>
+void launch_ingest(lpf_stream* s, const float* frame, int64_t slot) {
+    TS* dst = reinterpret_cast<TS*>(s->ring) + slot * s->F * s->P;
+    int vec = ((reinterpret_cast<uintptr_t>(frame) & 15u) == 0 && (s->HW % 4) == 0) ? 1 : 0;
+    int64_t work = vec ? s->F * s->HW / 4 : s->F * s->HW;
+    int blocks = (int)std::min<int64_t>((work + 255) / 256, 148 * 16);
+    lpf::k_ingest<TS><<<blocks, 256, 0, s->st>>>(frame, dst, s->F, s->HW, s->P, vec);
+}
+
+template <typename TS>
+void launch_dedisperse(lpf_stream* s, int n_rows, int Tmod) {
+    const int rpb = 8;
+    dim3 grid((unsigned)((s->P / 4 + 255) / 256), (unsigned)((n_rows + rpb - 1) / rpb));
+    size_t smem = (size_t)rpb * s->F * sizeof(int64_t);
+    lpf::k_dedisperse<TS><<<grid, 256, smem, s->st>>>(reinterpret_cast<const TS*>(s->ring), s->D,
+                                                      s->d_lag, s->F, s->depth, Tmod, n_rows, rpb, s->P);
+}
+
+template <typename TS>
+void launch_dynspec(lpf_stream* s, int n, int Tw, int slot_first, float* out) {
+    int64_t total = (int64_t)n * s->F * Tw;
+    int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 32);
+    if (blocks < 1) blocks = 1;
+    lpf::k_dynspec<TS><<<blocks, 256, 0, s->st>>>(reinterpret_cast<const TS*>(s->ring), s->d_yx, n,
+                                                  s->F, Tw, s->depth, slot_first, s->P, s->H, s->W,
+                                                  s->prm.dyn_box_r, out);
+}
+
+size_t filter_smem_bytes(int r, int rmax) {
+    auto odd = [](int n) { return n | 1; };
+    int RY = lpf::kTile + 4 * r, nC = lpf::kTile + 2 * r;
+    size_t floats = (size_t)RY * odd(RY) + (size_t)RY * odd(nC) + 2 * (size_t)nC * odd(nC) +
+                    (size_t)(nC + 2 * rmax + 2) * odd(lpf::kTile);
+    return floats * sizeof(float);
+}
+
+void prof_mark(lpf_stream* s, int sl, int i) {
+    if (s->profiling) cudaEventRecord(s->ev[sl][i], s->st);
+}
+
+// Accumulate the stage times of a finished slot (its done event has completed).
+void prof_collect(lpf_stream* s, int sl) {
+    if (!s->prof_slot[sl]) return;
+    for (int i = 0; i < ST_N; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, s->ev[sl][i], s->ev[sl][i + 1]) == cudaSuccess) {
+            s->prof_ms[i] += ms;
+            s->prof_n[i] += 1;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    s->prof_slot[sl] = false;
+}
+
+int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
+    const int sl = s->next_slot;
+    Slot& slot = s->slots[sl];
+    const int64_t ring_slot = T % s->depth;
+    const int Tmod = (int)ring_slot;
+    const int n_rows = n_active_rows(s, T);
+    cudaGetLastError();
+
+    prof_mark(s, sl, ST_INGEST);
+    switch (s->prm.dtype) {
+        case LPF_FP32: launch_ingest<float>(s, frame_dev, ring_slot); break;
+        case LPF_FP16: launch_ingest<__half>(s, frame_dev, ring_slot); break;
+        default: launch_ingest<__nv_bfloat16>(s, frame_dev, ring_slot); break;
+    }
+    lpf::k_zero_u32<<<1, 32, 0, s->st>>>(s->d_counter, 1);
+    prof_mark(s, sl, ST_DEDISP);
+    if (n_rows > 0) {
+        switch (s->prm.dtype) {
+            case LPF_FP32: launch_dedisperse<float>(s, n_rows, Tmod); break;
+            case LPF_FP16: launch_dedisperse<__half>(s, n_rows, Tmod); break;
+            default: launch_dedisperse<__nv_bfloat16>(s, n_rows, Tmod); break;
+        }
+    }
+    prof_mark(s, sl, ST_FILTER);
+    if (n_rows > 0) {
+        lpf::FilterArgs a;
+        a.D = s->D; a.P = s->P; a.H = s->H; a.W = s->W; a.r = s->prm.box_r; a.kappa = s->prm.kappa;
+        a.tiles_x = s->tiles_x; a.tiles_y = s->tiles_y;
+        a.member_start = s->d_member_start; a.member_ord = s->d_member_ord;
+        a.keys = s->keys[0]; a.vals = s->vals[0]; a.counter = s->d_counter; a.cap = s->prm.cand_cap;
+        a.bx = s->bx; a.by = s->by; a.partials = s->d_partials;
+        dim3 grid((unsigned)(s->tiles_x * s->tiles_y), (unsigned)n_rows);
+        if (s->filter_rmax == 8)
+            lpf::k_filter<8><<<grid, lpf::kFilterThreads, s->filter_smem, s->st>>>(a);
+        else
+            lpf::k_filter<16><<<grid, lpf::kFilterThreads, s->filter_smem, s->st>>>(a);
+    }
+    prof_mark(s, sl, ST_SORT);
+    int cur = 0;
+    for (int shift = 0; shift < s->key_bits; shift += 8) {
+        lpf::k_rs_hist<<<kSortBlocks, lpf::kSortThreads, 0, s->st>>>(s->keys[cur], s->d_counter,
+                                                                       s->prm.cand_cap, shift, s->d_hist);
+        lpf::k_rs_scan<<<1, 1024, 0, s->st>>>(s->d_hist, 256 * kSortBlocks);
+        lpf::k_rs_scatter<<<kSortBlocks, lpf::kSortThreads, 0, s->st>>>(
+            s->keys[cur], s->vals[cur], s->keys[cur ^ 1], s->vals[cur ^ 1], s->d_counter,
+            s->prm.cand_cap, shift, s->d_hist);
+        cur ^= 1;
+    }
+    prof_mark(s, sl, ST_FORMAT);
+    lpf::k_format<<<148 * 4, 256, 0, s->st>>>(s->keys[cur], s->vals[cur], s->d_counter, s->prm.cand_cap,
+                                              slot.d_out, s->d_ord2d, s->d_dmax, T, s->bx, s->by);
+    prof_mark(s, sl, ST_STATS);
+    if (n_rows > 0)
+        lpf::k_stats<<<n_rows, 256, 0, s->st>>>(s->d_partials, s->tiles_x * s->tiles_y, slot.d_stats);
+    prof_mark(s, sl, ST_N);
+    if (cudaGetLastError() != cudaSuccess) return LPF_E_CUDA;
+    LPF_TRY(cudaMemcpyAsync(s->h_count + sl, s->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st));
+    if (n_rows > 0)
+        LPF_TRY(cudaMemcpyAsync(s->h_stats + (size_t)sl * s->n_distinct * 3, slot.d_stats,
+                                (size_t)n_rows * 3 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    LPF_TRY(cudaEventRecord(slot.done, s->st));
+    s->prof_slot[sl] = s->profiling;
+    slot.T = T;
+    slot.n_active = n_rows;
+    s->pending.push_back(sl);
+    s->next_slot = (sl + 1) % s->n_slots;
+    if (!s->any_push) {
+        s->any_push = true;
+        s->T_first = T;
+    }
+    s->last_T = T;
+    s->frames_pushed += 1;
+    return LPF_OK;
+}
+
+int check_push(lpf_stream* s, int64_t T) {
+    if (!s || T < 0) return LPF_E_ARG;
+    if (s->any_push && T != s->last_T + 1) return LPF_E_ORDER;
+    if ((int)s->pending.size() >= s->n_slots) return LPF_E_BUSY;
+    return LPF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lpf_default_params(lpf_params* p) {
+    if (!p) return;
+    p->cadence_s = 1.0;
+    p->kappa = 6.0f;
+    p->box_r = 15;
+    p->lmax_r = 1;
+    p->dtype = LPF_FP32;
+    p->cand_cap = 1 << 20;
+    p->dyn_box_r = 0;
+    p->result_slots = 2;
+    p->cuda_stream = nullptr;
+}
+
+const char* lpf_strerror(int code) {
+    switch (code) {
+        case LPF_OK: return "ok";
+        case LPF_E_ARG: return "invalid argument";
+        case LPF_E_DEPTH: return "buffer depth too small for the delay table or window";
+        case LPF_E_ORDER: return "frame index out of order";
+        case LPF_E_OOM: return "out of memory";
+        case LPF_E_BUDGET: return "stream exceeds the HBM budget";
+        case LPF_E_TRUNCATED: return "candidate list truncated";
+        case LPF_E_STALE: return "frames no longer in the ring buffer";
+        case LPF_E_TIMEOUT: return "timed out";
+        case LPF_E_CUDA: return "CUDA error";
+        case LPF_E_BUSY: return "all result slots are unpolled";
+        case LPF_E_NODATA: return "no frame to poll";
+        default: return "unknown error";
+    }
+}
+
+int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, int n_dm,
+                    const double* dm_grid, int buffer_depth, const lpf_params* params) {
+    if (!out) return LPF_E_ARG;
+    *out = nullptr;
+    lpf_params prm;
+    lpf_default_params(&prm);
+    if (params) prm = *params;
+    if (H <= 0 || W <= 0 || F <= 0 || n_dm <= 0 || !freqs_mhz || !dm_grid || buffer_depth <= 0)
+        return LPF_E_ARG;
+    if (H > (1 << 16) || W > (1 << 16) || buffer_depth > 32767) return LPF_E_ARG;
+    if (!(prm.cadence_s > 0) || prm.box_r < 1 || prm.box_r > 16 || prm.lmax_r != 1) return LPF_E_ARG;
+    if (prm.dtype < LPF_FP32 || prm.dtype > LPF_BF16 || prm.cand_cap < 1 || prm.dyn_box_r < 0) return LPF_E_ARG;
+    if (prm.result_slots < 1 || prm.result_slots > kMaxSlots) return LPF_E_ARG;
+    if (!std::isfinite(prm.kappa)) return LPF_E_ARG;
+    for (int f = 0; f < F; ++f)
+        if (!(freqs_mhz[f] > 0) || !std::isfinite(freqs_mhz[f])) return LPF_E_ARG;
+    for (int d = 0; d < n_dm; ++d)
+        if (!(dm_grid[d] >= 0) || !std::isfinite(dm_grid[d])) return LPF_E_ARG;
+
+    lpf_stream* s = new (std::nothrow) lpf_stream();
+    if (!s) return LPF_E_OOM;
+    s->H = H; s->W = W; s->F = F; s->n_dm = n_dm; s->depth = buffer_depth; s->prm = prm;
+    s->HW = (int64_t)H * W;
+    s->P = (s->HW + 7) / 8 * 8;
+    s->elem = prm.dtype == LPF_FP32 ? 4 : 2;
+    s->n_slots = prm.result_slots;
+    build_delay_table(s, freqs_mhz, dm_grid);
+    if (buffer_depth < s->max_delay + 1) {
+        delete s;
+        return LPF_E_DEPTH;
+    }
+    build_plan(s);
+    s->bx = std::max(1, ceil_log2(W));
+    s->by = std::max(1, ceil_log2(H));
+    s->bo = std::max(1, ceil_log2(n_dm));
+    s->key_bits = s->bx + s->by + s->bo;
+    if (s->key_bits > 64) {
+        delete s;
+        return LPF_E_ARG;
+    }
+    s->tiles_x = (W + lpf::kTile - 1) / lpf::kTile;
+    s->tiles_y = (H + lpf::kTile - 1) / lpf::kTile;
+    s->filter_rmax = prm.box_r <= 8 ? 8 : 16;
+    s->filter_smem = filter_smem_bytes(prm.box_r, s->filter_rmax);
+
+    int rc = LPF_OK;
+    if (cudaGetDevice(&s->dev) != cudaSuccess) { cudaGetLastError(); delete s; return LPF_E_CUDA; }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) { cudaGetLastError(); delete s; return LPF_E_CUDA; }
+    if (prm.cuda_stream) {
+        s->st = (cudaStream_t)prm.cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess) { delete s; return LPF_E_CUDA; }
+        s->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&s->copy_st, cudaStreamNonBlocking) != cudaSuccess) rc = LPF_E_CUDA;
+    if (rc == LPF_OK && cudaFuncSetAttribute(lpf::k_filter<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)filter_smem_bytes(8, 8)) != cudaSuccess) rc = LPF_E_CUDA;
+    if (rc == LPF_OK && cudaFuncSetAttribute(lpf::k_filter<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)filter_smem_bytes(16, 16)) != cudaSuccess) rc = LPF_E_CUDA;
+    const size_t ring_elems = (size_t)buffer_depth * F * s->P;
+    if (rc == LPF_OK) {
+        if (cudaMalloc(&s->ring, ring_elems * s->elem) != cudaSuccess) { cudaGetLastError(); rc = LPF_E_OOM; }
+        else s->device_bytes += ring_elems * s->elem;
+    }
+    if (rc == LPF_OK && cudaMemsetAsync(s->ring, 0, ring_elems * s->elem, s->st) != cudaSuccess) rc = LPF_E_CUDA;
+    if (rc == LPF_OK) rc = dev_alloc(s, &s->D, (size_t)s->n_distinct * s->P);
+    if (rc == LPF_OK) rc = dev_alloc(s, &s->stage, (size_t)F * s->HW);
+    if (rc == LPF_OK) rc = dev_alloc(s, &s->d_lag, (size_t)s->n_distinct * F);
+    if (rc == LPF_OK) rc = dev_alloc(s, &s->d_member_start, s->member_start.size());
+    if (rc == LPF_OK) rc = dev_alloc(s, &s->d_member_ord, s->member_ord.size());
+    if (rc == LPF_OK) rc = dev_alloc(s, &s->d_ord2d, (size_t)n_dm);
+    if (rc == LPF_OK) rc = dev_alloc(s, &s->d_dmax, (size_t)n_dm);
+    for (int i = 0; i < 2 && rc == LPF_OK; ++i) {
+        rc = dev_alloc(s, &s->keys[i], (size_t)prm.cand_cap);
+        if (rc == LPF_OK) rc = dev_alloc(s, &s->vals[i], (size_t)prm.cand_cap);
+    }
+    if (rc == LPF_OK) rc = dev_alloc(s, &s->d_counter, 4);
+    if (rc == LPF_OK) rc = dev_alloc(s, &s->d_hist, (size_t)256 * kSortBlocks);
+    if (rc == LPF_OK) rc = dev_alloc(s, &s->d_partials, (size_t)s->n_distinct * s->tiles_x * s->tiles_y * 3);
+    for (int i = 0; i < s->n_slots && rc == LPF_OK; ++i) {
+        rc = dev_alloc(s, &s->slots[i].d_out, (size_t)prm.cand_cap);
+        if (rc == LPF_OK) rc = dev_alloc(s, &s->slots[i].d_stats, (size_t)s->n_distinct * 3);
+        if (rc == LPF_OK && cudaEventCreateWithFlags(&s->slots[i].done, cudaEventDisableTiming) != cudaSuccess)
+            rc = LPF_E_CUDA;
+    }
+    for (int k = 0; k < s->n_slots && rc == LPF_OK; ++k)
+        for (int i = 0; i <= ST_N && rc == LPF_OK; ++i)
+            if (cudaEventCreate(&s->ev[k][i]) != cudaSuccess) rc = LPF_E_CUDA;
+    if (rc == LPF_OK) {
+        if (cudaMallocHost(&s->h_count, sizeof(unsigned) * kMaxSlots) != cudaSuccess ||
+            cudaMallocHost(&s->h_stats, sizeof(double) * kMaxSlots * s->n_distinct * 3) != cudaSuccess) {
+            cudaGetLastError();
+            rc = LPF_E_OOM;
+        }
+    }
+    if (rc == LPF_OK) {
+        std::vector<int16_t> lag((size_t)s->n_distinct * F);
+        for (int rr = 0; rr < s->n_distinct; ++rr) {
+            int d = s->ord2d[s->member_ord[s->member_start[rr]]];
+            for (int f = 0; f < F; ++f)
+                lag[(size_t)rr * F + f] = (int16_t)(s->dmax[d] - s->delay[(size_t)d * F + f]);
+        }
+        std::vector<int> dm32(s->dmax.begin(), s->dmax.end());
+        if (cudaMemcpy(s->d_lag, lag.data(), lag.size() * sizeof(int16_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(s->d_member_start, s->member_start.data(), s->member_start.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(s->d_member_ord, s->member_ord.data(), s->member_ord.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(s->d_ord2d, s->ord2d.data(), s->ord2d.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(s->d_dmax, dm32.data(), dm32.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaStreamSynchronize(s->st) != cudaSuccess)
+            rc = LPF_E_CUDA;
+    }
+    if (rc != LPF_OK) {
+        free_all(s);
+        delete s;
+        return rc;
+    }
+    s->last_stats.assign((size_t)n_dm * 2, std::nan(""));
+    *out = s;
+    return LPF_OK;
+}
+
+int lpf_push_frame(lpf_stream* s, const float* frame_dev, int64_t T) {
+    int rc = check_push(s, T);
+    if (rc != LPF_OK) return rc;
+    if (!frame_dev) return LPF_E_ARG;
+    if (cudaSetDevice(s->dev) != cudaSuccess) return LPF_E_CUDA;
+    return enqueue_push(s, frame_dev, T);
+}
+
+int lpf_push_frame_host(lpf_stream* s, const float* frame_host, int64_t T) {
+    int rc = check_push(s, T);
+    if (rc != LPF_OK) return rc;
+    if (!frame_host) return LPF_E_ARG;
+    if (cudaSetDevice(s->dev) != cudaSuccess) return LPF_E_CUDA;
+    LPF_TRY(cudaMemcpyAsync(s->stage, frame_host, sizeof(float) * s->F * s->HW, cudaMemcpyHostToDevice, s->st));
+    return enqueue_push(s, s->stage, T);
+}
+
+int lpf_poll_candidates(lpf_stream* s, lpf_candidate* out_host, int cap, int* n_out, int64_t* T_out,
+                        int timeout_ms) {
+    if (!s || cap < 0 || (cap > 0 && !out_host)) return LPF_E_ARG;
+    if (s->pending.empty()) return LPF_E_NODATA;
+    if (cudaSetDevice(s->dev) != cudaSuccess) return LPF_E_CUDA;
+    const int sl = s->pending.front();
+    Slot& slot = s->slots[sl];
+    auto t_start = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t q = cudaEventQuery(slot.done);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return LPF_E_CUDA;
+        if (timeout_ms >= 0) {
+            double el = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+            if (el >= timeout_ms) return LPF_E_TIMEOUT;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    prof_collect(s, sl);
+    const unsigned found = s->h_count[sl];
+    const unsigned stored = std::min<unsigned>(found, (unsigned)s->prm.cand_cap);
+    const unsigned ncopy = std::min<unsigned>(stored, (unsigned)cap);
+    if (ncopy > 0) {
+        LPF_TRY(cudaMemcpyAsync(out_host, slot.d_out, (size_t)ncopy * sizeof(lpf_candidate),
+                                cudaMemcpyDeviceToHost, s->copy_st));
+        LPF_TRY(cudaStreamSynchronize(s->copy_st));
+    }
+    // stats of this frame
+    std::fill(s->last_stats.begin(), s->last_stats.end(), std::nan(""));
+    const double* hs = s->h_stats + (size_t)sl * s->n_distinct * 3;
+    for (int rr = 0; rr < slot.n_active; ++rr) {
+        double n = hs[rr * 3 + 2];
+        double mean = n > 0 ? hs[rr * 3 + 0] / n : 0.0;
+        double rms = n > 0 ? std::sqrt(hs[rr * 3 + 1] / n) : 0.0;
+        for (int m = s->member_start[rr]; m < s->member_start[rr + 1]; ++m) {
+            int d = s->ord2d[s->member_ord[m]];
+            s->last_stats[(size_t)d * 2] = mean;
+            s->last_stats[(size_t)d * 2 + 1] = rms;
+        }
+    }
+    if (n_out) *n_out = (int)found;
+    if (T_out) *T_out = slot.T;
+    s->polled = true;
+    s->polled_T = slot.T;
+    s->polled_slot = sl;
+    s->pending.pop_front();
+    if (found > (unsigned)s->prm.cand_cap || found > (unsigned)cap) return LPF_E_TRUNCATED;
+    return LPF_OK;
+}
+
+int lpf_extract_dynspec(lpf_stream* s, const lpf_candidate* c_host, int n, int Tw, float* out_dev) {
+    if (!s || n < 0 || Tw < 1 || (n > 0 && (!c_host || !out_dev))) return LPF_E_ARG;
+    if (Tw > s->depth) return LPF_E_DEPTH;
+    if (!s->polled) return LPF_E_NODATA;
+    const int64_t T = s->polled_T;
+    if (T - Tw + 1 < s->T_first) return LPF_E_STALE;
+    if (s->last_T - s->depth + 1 > T - Tw + 1) return LPF_E_STALE;
+    if (n == 0) return LPF_OK;
+    std::vector<int2> yx(n);
+    for (int i = 0; i < n; ++i) {
+        if (c_host[i].y < 0 || c_host[i].y >= s->H || c_host[i].x < 0 || c_host[i].x >= s->W) return LPF_E_ARG;
+        yx[i] = make_int2(c_host[i].y, c_host[i].x);
+    }
+    if (cudaSetDevice(s->dev) != cudaSuccess) return LPF_E_CUDA;
+    if (n > s->yx_cap) {
+        LPF_TRY(cudaStreamSynchronize(s->st));
+        if (s->d_yx) { cudaFree(s->d_yx); s->device_bytes -= (size_t)s->yx_cap * sizeof(int2); }
+        s->d_yx = nullptr;
+        s->yx_cap = 0;
+        int rc = dev_alloc(s, &s->d_yx, (size_t)n);
+        if (rc != LPF_OK) return rc;
+        s->yx_cap = n;
+    }
+    LPF_TRY(cudaMemcpyAsync(s->d_yx, yx.data(), (size_t)n * sizeof(int2), cudaMemcpyHostToDevice, s->st));
+    int slot_first = (int)((T - Tw + 1) % s->depth);
+    cudaGetLastError();
+    switch (s->prm.dtype) {
+        case LPF_FP32: launch_dynspec<float>(s, n, Tw, slot_first, out_dev); break;
+        case LPF_FP16: launch_dynspec<__half>(s, n, Tw, slot_first, out_dev); break;
+        default: launch_dynspec<__nv_bfloat16>(s, n, Tw, slot_first, out_dev); break;
+    }
+    if (cudaGetLastError() != cudaSuccess) return LPF_E_CUDA;
+    // the pageable coordinate vector must outlive the copy
+    LPF_TRY(cudaStreamSynchronize(s->st));
+    return LPF_OK;
+}
+
+int lpf_get_delay_table(const lpf_stream* s, int32_t* out) {
+    if (!s || !out) return LPF_E_ARG;
+    std::memcpy(out, s->delay.data(), s->delay.size() * sizeof(int32_t));
+    return LPF_OK;
+}
+
+int lpf_get_stats(const lpf_stream* s, double* out) {
+    if (!s || !out) return LPF_E_ARG;
+    if (!s->polled) return LPF_E_NODATA;
+    std::memcpy(out, s->last_stats.data(), s->last_stats.size() * sizeof(double));
+    return LPF_OK;
+}
+
+int lpf_stream_info(const lpf_stream* s, lpf_stream_info_t* out) {
+    if (!s || !out) return LPF_E_ARG;
+    out->H = s->H; out->W = s->W; out->F = s->F; out->n_dm = s->n_dm; out->depth = s->depth;
+    out->dtype = s->prm.dtype; out->n_distinct = s->n_distinct; out->max_delay = s->max_delay;
+    out->ring_bytes = (size_t)s->depth * s->F * s->P * s->elem;
+    out->device_bytes = s->device_bytes;
+    out->frames_pushed = s->frames_pushed;
+    out->last_T = s->last_T;
+    return LPF_OK;
+}
+
+int lpf_stream_sync(lpf_stream* s) {
+    if (!s) return LPF_E_ARG;
+    if (cudaSetDevice(s->dev) != cudaSuccess) return LPF_E_CUDA;
+    return cuda_fail(cudaStreamSynchronize(s->st));
+}
+
+int lpf_stream_close(lpf_stream* s) {
+    if (!s) return LPF_OK;
+    free_all(s);
+    delete s;
+    return LPF_OK;
+}
+
+int lpf_set_profiling(lpf_stream* s, int on) {
+    if (!s) return LPF_E_ARG;
+    s->profiling = on != 0;
+    return LPF_OK;
+}
+
+int lpf_get_kernel_times(lpf_stream* s, const char** names, double* total_ms, int64_t* launches, int n,
+                         int reset) {
+    if (!s) return LPF_E_ARG;
+    for (int i = 0; i < ST_N && i < n; ++i) {
+        if (names) names[i] = kStageNames[i];
+        if (total_ms) total_ms[i] = s->prof_ms[i];
+        if (launches) launches[i] = s->prof_n[i];
+    }
+    if (reset)
+        for (int i = 0; i < ST_N; ++i) { s->prof_ms[i] = 0; s->prof_n[i] = 0; }
+    return ST_N;
+}
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+"""The C-ABI library builds, loads and exports every symbol include/lpf.h declares.
+
+No compute call is made here (no GPU on this host); only argument validation
+that returns before any CUDA call is exercised.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2103_15418_b300 as lpf
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "lpf.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lpf_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = lpf.load()
+    names = declared_symbols()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(lpf.EXPORTS)
+
+
+def test_struct_layouts():
+    assert ctypes.sizeof(lpf.Candidate) == 24
+    assert lpf.CANDIDATE_DTYPE.itemsize == 24
+    p = lpf.default_params()
+    assert (p.cadence_s, p.kappa, p.box_r, p.lmax_r, p.dtype) == (1.0, 6.0, 15, 1, 0)
+    assert p.cand_cap == 1 << 20 and p.result_slots == 2 and not p.cuda_stream
+
+
+def test_strerror_names_every_code():
+    lib = lpf.load()
+    for code in range(0, -12, -1):
+        assert lib.lpf_strerror(code).decode() not in ("", "unknown error")
+    assert lib.lpf_strerror(-99).decode() == "unknown error"
+
+
+def test_argument_validation_before_any_cuda_call():
+    f = np.array([60.0, 61.0])
+    dm = np.array([0.0, 10.0])
+    bad = [
+        dict(H=0, W=8, freqs_mhz=f, dm_grid=dm, depth=8),
+        dict(H=8, W=8, freqs_mhz=np.array([60.0, -1.0]), dm_grid=dm, depth=8),
+        dict(H=8, W=8, freqs_mhz=f, dm_grid=np.array([-1.0]), depth=8),
+        dict(H=8, W=8, freqs_mhz=f, dm_grid=dm, depth=8, box_r=17),
+        dict(H=8, W=8, freqs_mhz=f, dm_grid=dm, depth=8, box_r=0),
+        dict(H=8, W=8, freqs_mhz=f, dm_grid=dm, depth=8, cadence_s=0.0),
+        dict(H=8, W=8, freqs_mhz=f, dm_grid=dm, depth=8, result_slots=0),
+    ]
+    for kw in bad:
+        with pytest.raises(lpf.LpfError) as e:
+            lpf.Stream(**kw)
+        assert e.value.code == lpf.LPF_E_ARG, kw
+    # depth shorter than the largest delay + 1 (DM 400 over 60-61 MHz is ~30 s)
+    with pytest.raises(lpf.LpfError) as e:
+        lpf.Stream(8, 8, f, np.array([0.0, 400.0]), 4)
+    assert e.value.code == lpf.LPF_E_DEPTH
+
+
+def test_null_handles_are_rejected():
+    lib = lpf.load()
+    assert lib.lpf_push_frame(None, None, 0) == lpf.LPF_E_ARG
+    assert lib.lpf_poll_candidates(None, None, 0, None, None, 0) == lpf.LPF_E_ARG
+    assert lib.lpf_stream_close(None) == lpf.LPF_OK
