@@ -71,6 +71,8 @@ typedef struct {
     int    dyn_box_r;     /* dynspec box radius (0 = the candidate pixel)         default 0     */
     int    result_slots;  /* frames that may be pushed but not yet polled, 1..16  default 2     */
     void*  cuda_stream;   /* cudaStream_t to run on; NULL = a private non-blocking stream    */
+    int    filter_impl;   /* 0 = auto (streaming kernel when box_r is 7 or 15, else tiled),
+                             1 = tiled kernel, 2 = streaming kernel (box_r 7 or 15 only)      */
 } lpf_params;
 
 /* One candidate: pixel (y, x) of DM trial dm_idx (index into dm_grid) whose
@@ -105,7 +107,7 @@ void lpf_default_params(lpf_params* p);
  * on the host (Sec. 3.2) and allocates the ring buffer and scratch on the
  * current CUDA device.
  * Errors: LPF_E_ARG (sizes <= 0, box_r outside 1..16, lmax_r != 1, bad dtype,
- * non-positive frequency or cadence, negative DM), LPF_E_DEPTH (buffer_depth <
+ * non-positive frequency or cadence, negative DM, filter_impl 2 with another box_r), LPF_E_DEPTH (buffer_depth <
  * max delay + 1), LPF_E_OOM, LPF_E_CUDA (no device).
  */
 int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_mhz,

@@ -36,7 +36,7 @@ EXPORTS = [
 class Params(Structure):
     _fields_ = [("cadence_s", c_double), ("kappa", c_float), ("box_r", c_int), ("lmax_r", c_int),
                 ("dtype", c_int), ("cand_cap", c_int), ("dyn_box_r", c_int),
-                ("result_slots", c_int), ("cuda_stream", c_void_p)]
+                ("result_slots", c_int), ("cuda_stream", c_void_p), ("filter_impl", c_int)]
 
 
 class Candidate(Structure):
@@ -113,7 +113,8 @@ class Stream:
 
     def __init__(self, H: int, W: int, freqs_mhz, dm_grid, depth: int, *, cadence_s: float = 1.0,
                  kappa: float = 6.0, box_r: int = 15, dtype: str = "fp32", cand_cap: int = 1 << 20,
-                 dyn_box_r: int = 0, result_slots: int = 2, cuda_stream=None):
+                 dyn_box_r: int = 0, result_slots: int = 2, cuda_stream=None,
+                 filter_impl: str = "auto"):
         lib = load()
         self.H, self.W = int(H), int(W)
         self.freqs = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
@@ -122,6 +123,7 @@ class Stream:
         p = default_params()
         p.cadence_s, p.kappa, p.box_r = cadence_s, kappa, box_r
         p.dtype, p.cand_cap, p.dyn_box_r, p.result_slots = DTYPES[dtype], cand_cap, dyn_box_r, result_slots
+        p.filter_impl = {"auto": 0, "tiled": 1, "streaming": 2}[filter_impl]
         if cuda_stream is not None:
             p.cuda_stream = int(getattr(cuda_stream, "cuda_stream", cuda_stream))
         self.params = p

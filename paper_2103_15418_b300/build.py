@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblpf.so")
 SOURCES = ["lpf_stream.cu"]
-HEADERS = ["lpf_kernels.cuh", os.path.join("..", "..", "include", "lpf.h")]
+HEADERS = ["lpf_kernels.cuh", "lpf_filter_stream.cuh", os.path.join("..", "..", "include", "lpf.h")]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",

@@ -8,6 +8,7 @@
 // and records an event; poll waits on that event with a deadline.
 #include "../../include/lpf.h"
 #include "lpf_kernels.cuh"
+#include "lpf_filter_stream.cuh"
 
 #include <algorithm>
 #include <chrono>
@@ -104,6 +105,8 @@ struct lpf_stream {
     int tiles_x = 0, tiles_y = 0;
     size_t filter_smem = 0;
     int filter_rmax = 16;
+    bool stream_filter = false;     // streaming column-strip kernel (box_r 7 or 15)
+    int n_strips = 0;
 
     bool profiling = false;
     cudaEvent_t ev[kMaxSlots][ST_N + 1] = {};
@@ -262,6 +265,10 @@ void launch_dynspec(lpf_stream* s, int n, int Tw, int slot_first, float* out) {
                                                   s->prm.dyn_box_r, out);
 }
 
+int n_filter_blocks(const lpf_stream* s) {
+    return s->stream_filter ? s->n_strips : s->tiles_x * s->tiles_y;
+}
+
 size_t filter_smem_bytes(int r, int rmax) {
     auto odd = [](int n) { return n | 1; };
     int RY = lpf::kTile + 4 * r, nC = lpf::kTile + 2 * r;
@@ -320,11 +327,19 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
         a.member_start = s->d_member_start; a.member_ord = s->d_member_ord;
         a.keys = s->keys[0]; a.vals = s->vals[0]; a.counter = s->d_counter; a.cap = s->prm.cand_cap;
         a.bx = s->bx; a.by = s->by; a.partials = s->d_partials;
-        dim3 grid((unsigned)(s->tiles_x * s->tiles_y), (unsigned)n_rows);
-        if (s->filter_rmax == 8)
-            lpf::k_filter<8><<<grid, lpf::kFilterThreads, s->filter_smem, s->st>>>(a);
-        else
-            lpf::k_filter<16><<<grid, lpf::kFilterThreads, s->filter_smem, s->st>>>(a);
+        if (s->stream_filter) {
+            dim3 grid((unsigned)s->n_strips, (unsigned)n_rows);
+            if (s->prm.box_r == 7)
+                lpf::k_filter_stream<7><<<grid, lpf::kStreamThreads, s->filter_smem, s->st>>>(a);
+            else
+                lpf::k_filter_stream<15><<<grid, lpf::kStreamThreads, s->filter_smem, s->st>>>(a);
+        } else {
+            dim3 grid((unsigned)(s->tiles_x * s->tiles_y), (unsigned)n_rows);
+            if (s->filter_rmax == 8)
+                lpf::k_filter<8><<<grid, lpf::kFilterThreads, s->filter_smem, s->st>>>(a);
+            else
+                lpf::k_filter<16><<<grid, lpf::kFilterThreads, s->filter_smem, s->st>>>(a);
+        }
     }
     prof_mark(s, sl, ST_SORT);
     int cur = 0;
@@ -342,7 +357,7 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
                                               slot.d_out, s->d_ord2d, s->d_dmax, T, s->bx, s->by);
     prof_mark(s, sl, ST_STATS);
     if (n_rows > 0)
-        lpf::k_stats<<<n_rows, 256, 0, s->st>>>(s->d_partials, s->tiles_x * s->tiles_y, slot.d_stats);
+        lpf::k_stats<<<n_rows, 256, 0, s->st>>>(s->d_partials, n_filter_blocks(s), slot.d_stats);
     prof_mark(s, sl, ST_N);
     if (cudaGetLastError() != cudaSuccess) return LPF_E_CUDA;
     LPF_TRY(cudaMemcpyAsync(s->h_count + sl, s->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st));
@@ -386,6 +401,7 @@ void lpf_default_params(lpf_params* p) {
     p->dyn_box_r = 0;
     p->result_slots = 2;
     p->cuda_stream = nullptr;
+    p->filter_impl = 0;
 }
 
 const char* lpf_strerror(int code) {
@@ -420,6 +436,8 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
     if (prm.dtype < LPF_FP32 || prm.dtype > LPF_BF16 || prm.cand_cap < 1 || prm.dyn_box_r < 0) return LPF_E_ARG;
     if (prm.result_slots < 1 || prm.result_slots > kMaxSlots) return LPF_E_ARG;
     if (!std::isfinite(prm.kappa)) return LPF_E_ARG;
+    if (prm.filter_impl < 0 || prm.filter_impl > 2) return LPF_E_ARG;
+    if (prm.filter_impl == 2 && prm.box_r != 7 && prm.box_r != 15) return LPF_E_ARG;
     for (int f = 0; f < F; ++f)
         if (!(freqs_mhz[f] > 0) || !std::isfinite(freqs_mhz[f])) return LPF_E_ARG;
     for (int d = 0; d < n_dm; ++d)
@@ -450,6 +468,10 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
     s->tiles_y = (H + lpf::kTile - 1) / lpf::kTile;
     s->filter_rmax = prm.box_r <= 8 ? 8 : 16;
     s->filter_smem = filter_smem_bytes(prm.box_r, s->filter_rmax);
+    s->stream_filter = prm.filter_impl == 2 || (prm.filter_impl == 0 && (prm.box_r == 7 || prm.box_r == 15));
+    s->n_strips = (W + lpf::kStreamTX - 1) / lpf::kStreamTX;
+    if (s->stream_filter)
+        s->filter_smem = (prm.box_r == 7 ? lpf::StreamGeom<7>::smem_floats : lpf::StreamGeom<15>::smem_floats) * sizeof(float);
 
     int rc = LPF_OK;
     if (cudaGetDevice(&s->dev) != cudaSuccess) { cudaGetLastError(); delete s; return LPF_E_CUDA; }
@@ -466,6 +488,10 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
                                             (int)filter_smem_bytes(8, 8)) != cudaSuccess) rc = LPF_E_CUDA;
     if (rc == LPF_OK && cudaFuncSetAttribute(lpf::k_filter<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)filter_smem_bytes(16, 16)) != cudaSuccess) rc = LPF_E_CUDA;
+    if (rc == LPF_OK && cudaFuncSetAttribute(lpf::k_filter_stream<7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(lpf::StreamGeom<7>::smem_floats * sizeof(float))) != cudaSuccess) rc = LPF_E_CUDA;
+    if (rc == LPF_OK && cudaFuncSetAttribute(lpf::k_filter_stream<15>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(lpf::StreamGeom<15>::smem_floats * sizeof(float))) != cudaSuccess) rc = LPF_E_CUDA;
     const size_t ring_elems = (size_t)buffer_depth * F * s->P;
     if (rc == LPF_OK) {
         if (cudaMalloc(&s->ring, ring_elems * s->elem) != cudaSuccess) { cudaGetLastError(); rc = LPF_E_OOM; }
@@ -485,7 +511,7 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
     }
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_counter, 4);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_hist, (size_t)256 * kSortBlocks);
-    if (rc == LPF_OK) rc = dev_alloc(s, &s->d_partials, (size_t)s->n_distinct * s->tiles_x * s->tiles_y * 3);
+    if (rc == LPF_OK) rc = dev_alloc(s, &s->d_partials, (size_t)s->n_distinct * n_filter_blocks(s) * 3);
     for (int i = 0; i < s->n_slots && rc == LPF_OK; ++i) {
         rc = dev_alloc(s, &s->slots[i].d_out, (size_t)prm.cand_cap);
         if (rc == LPF_OK) rc = dev_alloc(s, &s->slots[i].d_stats, (size_t)s->n_distinct * 3);

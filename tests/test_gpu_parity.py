@@ -59,10 +59,11 @@ def test_aartfaac_bands_256px(lib, dtype):
                 assert res["matched"] > 0
 
 
-def test_ragged_sizes_and_small_box(lib):
-    """Image not a multiple of the tile or of 4 pixels, 5 subbands, r = 5."""
+@pytest.mark.parametrize("r", [5, 7])
+def test_ragged_sizes_and_small_box(lib, r):
+    """Image not a multiple of the tile/strip or of 4 pixels, 5 subbands (tiled r=5, streaming r=7)."""
     spec = synth.spec_tiny(H=70, W=93, freqs_mhz=synth.subband_centres([60.0], 5),
-                           dm_grid=np.arange(0, 40, 3, dtype=np.float64), depth=12, box_r=5,
+                           dm_grid=np.arange(0, 40, 3, dtype=np.float64), depth=12, box_r=r,
                            kappa=4.0, n_sources=4)
     st = synth.SyntheticStream(spec, seed=9)
     fa = cached_frames(st)
@@ -87,6 +88,22 @@ def test_box_radius_extremes(lib, r):
             _push(s, st, T)
             _, c, _, _ = s.poll(timeout_ms=60000)
             compare_push(c, fa, T, delays, r, spec.kappa, gpu_stats=s.stats())
+
+
+@pytest.mark.parametrize("impl", ["tiled", "streaming"])
+def test_filter_kernels_agree_at_r15(lib, impl):
+    """Both filter kernels on the AARTFAAC bands at 320x288 (strip and tile tails), kappa 4."""
+    spec = synth.spec_aartfaac(H=320, W=288, n_sources=60, n_pulses=4, n_frames=52, kappa=4.0)
+    st = synth.SyntheticStream(spec, seed=17)
+    fa = cached_frames(st)
+    delays = O.delay_table(spec.freqs_mhz, spec.dm_grid, spec.cadence_s)
+    with _open(lib, spec, filter_impl=impl) as s:
+        for T in range(49):
+            _push(s, st, T)
+            _, c, n, trunc = s.poll(timeout_ms=60000)
+        res = compare_push(c, fa, 48, delays, spec.box_r, spec.kappa, dms=[0, 3, 50, 120, 200, 250],
+                           gpu_stats=s.stats())
+        assert res["matched"] > 100
 
 
 def test_aartfaac_full_size_sampled_trials(lib):
