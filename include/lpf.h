@@ -106,7 +106,8 @@ void lpf_default_params(lpf_params* p);
  * every input; the caller keeps nothing alive.  Builds the delay table in FP64
  * on the host (Sec. 3.2) and allocates the ring buffer and scratch on the
  * current CUDA device.
- * Errors: LPF_E_ARG (sizes <= 0, box_r outside 1..16, lmax_r != 1, bad dtype,
+ * F is at most 32, H and W at most 65536, buffer_depth at most 32767.
+ * Errors: LPF_E_ARG (sizes <= 0 or above those limits, box_r outside 1..16, lmax_r != 1, bad dtype,
  * non-positive frequency or cadence, negative DM, filter_impl 2 with another box_r), LPF_E_DEPTH (buffer_depth <
  * max delay + 1), LPF_E_OOM, LPF_E_CUDA (no device).
  */

@@ -3,7 +3,8 @@
 // One CTA owns a strip of TX = 128 output columns of one dedispersed image and
 // walks down it in blocks of 32 rows, so rows are never recomputed (only the
 // 2R-column halo of the strip is).  Per block:
-//   1. D rows of the block (strip + 2R halo each side) -> shared ring of 64 rows
+//   1. D rows of the next block (strip + 2R halo each side) are prefetched with
+//      cp.async into the other half of a double buffer while this block runs
 //   2. horizontal window sums of D ("two stacks", cancellation free)   -> hX
 //   3. per column: vertical sliding sum of hX -> C = sum / n, residual D - C
 //      stored in a shared ring of 64 rows
@@ -12,7 +13,9 @@
 //      snr = (D - C)/sqrt(S), threshold, 3x3 local maximum, stats, emission
 // The vertical pass of C runs R rows behind the input and that of S 2R rows
 // behind; the column thread that computes C for a column is the one that later
-// computes S for it, and the residual ring carries D - C across that lag.
+// computes S for it, and the residual ring carries D - C across that lag.  The
+// lagged reads of D itself (D at row yc for the residual, the 3x3 neighbours of
+// a candidate) go to global memory, where those rows are still L2-resident.
 // Out-of-image rows and columns contribute zeros, and C and S divide by the
 // in-image window count, which clips every window to the image (Sec. 2.1.1).
 #pragma once
@@ -36,6 +39,7 @@ struct StreamGeom {
     static constexpr int NR2 = (TX + L - 1) / L;         // runs per row, horizontal pass 2
     static constexpr int RR2 = (TX + NR2 - 1) / NR2;
     static constexpr size_t smem_floats = (size_t)64 * SD + (size_t)32 * SX + (size_t)64 * SX;
+    static constexpr int NLOAD = (32 * WD + kStreamThreads - 1) / kStreamThreads;
 };
 
 // out[c] = sum_{q=0..2R} in(c + q) for c in [c0, c0 + len), len <= RR <= 2R + 1,
@@ -75,13 +79,40 @@ __device__ __forceinline__ float inv_count(int y, int n) {
     return c == 2 * R + 1 ? 1.0f / (float)(2 * R + 1) : 1.0f / (float)c;
 }
 
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
+                 "r"(valid ? 4 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+// Issue the copies of D rows [ybase, ybase + 32) x cols [x0 - 2R, x0 + TX + 2R) into dst
+// (zero-filled outside the image).
+template <int R>
+__device__ __forceinline__ void load_block_async(float* dst, const float* Dimg, int ybase, int x0,
+                                                 int H, int W, int t) {
+    using G = StreamGeom<R>;
+#pragma unroll 4
+    for (int q = 0; q < G::NLOAD; ++q) {
+        int idx = t + q * kStreamThreads;
+        if (idx < 32 * G::WD) {
+            int j = idx / G::WD, c = idx - j * G::WD;
+            int y = ybase + j, x = x0 - 2 * R + c;
+            bool in = y < H && x >= 0 && x < W;
+            cp_async4(dst + j * G::SD + c, in ? Dimg + (int64_t)y * W + x : Dimg, in);
+        }
+    }
+}
+
 template <int R>
 __global__ void __launch_bounds__(kStreamThreads, 2) k_filter_stream(FilterArgs a) {
     using G = StreamGeom<R>;
     constexpr int TX = G::TX, WC = G::WC, WD = G::WD, SD = G::SD, SX = G::SX;
     constexpr int NT = kStreamThreads;
     extern __shared__ float sm[];
-    float* Dring = sm;                  // [64][SD]  D rows, ring by (y & 63); col = x - (x0 - 2R)
+    float* Dring = sm;                  // [2][32][SD] D rows of a block, double buffer; col = x - (x0 - 2R)
     float* hX = Dring + 64 * SD;        // [32][SX]  horizontal sums of the block
     float* Rring = hX + 32 * SX;        // [64][SX]  residual D - C; col = x - (x0 - R)
 
@@ -97,6 +128,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_filter_stream(FilterArgs 
     const bool xc_in = col_c && xc >= 0 && xc < W;
     const bool col_s = t >= R && t < R + TX && xc < W;
     const float inv_nx = xc_in ? inv_count<R>(xc, W) : 0.f;
+    const int nxc = xc_in ? min(xc + R, W - 1) - max(xc - R, 0) + 1 : 1;
 
     float histD[32], histE[32];
 #pragma unroll
@@ -106,26 +138,22 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_filter_stream(FilterArgs 
     const int m0 = a.member_start[row], nm = a.member_start[row + 1] - m0;
 
     const int nblk = (H + 2 * R + 31) / 32;
+    load_block_async<R>(Dring, Dimg, 0, x0, H, W, t);
+    cp_async_commit();
     for (int k = 0; k < nblk; ++k) {
         const int ybase = k * 32;
-        // ---- 1. D rows [ybase, ybase + 32) of the strip and its halo
-        {
-            float* Dblk = Dring + (k & 1) * 32 * SD;
-            for (int idx = t; idx < 32 * WD; idx += NT) {
-                int j = idx / WD, c = idx - j * WD;
-                int y = ybase + j, x = x0 - 2 * R + c;
-                float v = 0.f;
-                if (y < H && x >= 0 && x < W) v = __ldg(Dimg + (int64_t)y * W + x);
-                Dblk[j * SD + c] = v;
-            }
-        }
+        // ---- 1. prefetch block k + 1 into the other half, wait for block k
+        if (k + 1 < nblk)
+            load_block_async<R>(Dring + ((k + 1) & 1) * 32 * SD, Dimg, ybase + 32, x0, H, W, t);
+        cp_async_commit();
+        cp_async_wait_prev();
         __syncthreads();
         // ---- 2. hX[j][c] = sum of D over columns c .. c + 2R (ring cols) of row ybase + j
         for (int it = t; it < 32 * G::NR1; it += NT) {
             int j = it & 31, run = it >> 5;
             int c0 = run * G::RR1;
             int len = min(G::RR1, WC - c0);
-            const float* in = Dring + ((ybase + j) & 63) * SD;
+            const float* in = Dring + ((k & 1) * 32 + j) * SD;
             float* out = hX + j * SX;
             two_stack_run<R, G::RR1>(c0, len, [&](int c) { return in[c]; },
                                      [&](int c, float v) { out[c] = v; });
@@ -142,8 +170,10 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_filter_stream(FilterArgs 
                 const int yc = ybase + j - R;
                 float res = 0.f;
                 if (xc_in && yc >= 0 && yc < H) {
-                    float C = vD * (inv_count<R>(yc, H) * inv_nx);
-                    res = Dring[(yc & 63) * SD + (t + R)] - C;
+                    // correctly rounded division: C is exact when the window is constant
+                    int ny = min(yc + R, H - 1) - max(yc - R, 0) + 1;
+                    float C = __fdiv_rn(vD, (float)(ny * nxc));
+                    res = __ldg(Dimg + (int64_t)yc * W + xc) - C;
                 }
                 Rring[(yc & 63) * SX + t] = res;
             }
@@ -183,7 +213,8 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_filter_stream(FilterArgs 
                         s2 += snr * snr;
                         cnt += 1;
                         if (snr > a.kappa) {
-                            const float dv = Dring[(ys & 63) * SD + (t + R)];
+                            const float* p = Dimg + (int64_t)ys * W + xc;
+                            const float dv = __ldg(p);
                             bool mx = true;
 #pragma unroll
                             for (int dy = -1; dy <= 1; ++dy)
@@ -192,7 +223,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_filter_stream(FilterArgs 
                                     if (dy == 0 && dx == 0) continue;
                                     int yy = ys + dy, xx = xc + dx;
                                     if (yy >= 0 && yy < H && xx >= 0 && xx < W &&
-                                        Dring[((yy) & 63) * SD + (t + R + dx)] > dv)
+                                        __ldg(p + (int64_t)dy * W + dx) > dv)
                                         mx = false;
                                 }
                             cand = mx;

@@ -82,33 +82,39 @@ __global__ void k_ingest(const float* __restrict__ frame, TS* __restrict__ slot,
 
 // ------------------------------------------------------------------ a3: shift-sum
 // D[r][p] = sum_{f=0..F-1} ring[(Tmod - lag[r][f]) mod depth][f][p] for the
-// distinct delay rows r in [r0, r0 + rows_per_block) of this block's y index.
-// lag[r][f] = max_f delay - delay[r][f] (frames back from the newest frame).
-// Summation order is f = 0, 1, ..., F-1 in FP32.
-template <typename TS>
+// distinct delay rows r = 0 .. n_rows-1, lag[r][f] = max_f delay - delay[r][f]
+// (frames back from the newest frame).  Each thread owns 4 consecutive pixels
+// and walks every row in order: the current plane value of each subband stays
+// in registers and is reloaded only when the row's lag of that subband differs
+// from the previous row's (bit f of chg[r]).  The sum itself is formed afresh
+// for every row in the order f = 0, 1, ..., F-1 (FP32), so its rounding is
+// that of a plain F-term sum.
+template <int FMAX, typename TS>
 __global__ void __launch_bounds__(256) k_dedisperse(
-    const TS* __restrict__ ring, float* __restrict__ D, const int16_t* __restrict__ lag, int F,
-    int depth, int Tmod, int n_rows, int rows_per_block, int64_t P) {
-    extern __shared__ int64_t s_off[];   // [rows_per_block][F] element offsets of the planes
-    const int r0 = blockIdx.y * rows_per_block;
-    const int nr = min(rows_per_block, n_rows - r0);
-    for (int i = threadIdx.x; i < nr * F; i += blockDim.x) {
-        int r = i / F, f = i - r * F;
-        int slot = Tmod - (int)lag[(int64_t)(r0 + r) * F + f];
-        if (slot < 0) slot += depth;
-        s_off[i] = ((int64_t)slot * F + f) * P;
-    }
-    __syncthreads();
+    const TS* __restrict__ ring, float* __restrict__ D, const int16_t* __restrict__ lag,
+    const uint32_t* __restrict__ chg, int F, int depth, int Tmod, int n_rows, int64_t P) {
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (q >= P) return;
-    for (int r = 0; r < nr; ++r) {
-        const int64_t* off = s_off + r * F;
-        float4 acc = ld4(ring + off[0] + q);
-        for (int f = 1; f < F; ++f) {
-            float4 v = ld4(ring + off[f] + q);
-            acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    float4 cur[FMAX];
+#pragma unroll
+    for (int f = 0; f < FMAX; ++f) cur[f] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int r = 0; r < n_rows; ++r) {
+        const uint32_t m = __ldg(chg + r);
+        const int16_t* lr = lag + (int64_t)r * F;
+#pragma unroll
+        for (int f = 0; f < FMAX; ++f) {
+            if (f < F && ((m >> f) & 1u)) {
+                int slot = Tmod - (int)__ldg(lr + f);
+                if (slot < 0) slot += depth;
+                cur[f] = ld4(ring + ((int64_t)slot * F + f) * P + q);
+            }
         }
-        st4(D + (int64_t)(r0 + r) * P + q, acc);
+        float4 acc = cur[0];
+#pragma unroll
+        for (int f = 1; f < FMAX; ++f) {
+            if (f < F) { acc.x += cur[f].x; acc.y += cur[f].y; acc.z += cur[f].z; acc.w += cur[f].w; }
+        }
+        st4(D + (int64_t)r * P + q, acc);
     }
 }
 

@@ -70,6 +70,7 @@ struct lpf_stream {
     float* D = nullptr;
     float* stage = nullptr;          // host-push staging frame
     int16_t* d_lag = nullptr;
+    uint32_t* d_chg = nullptr;      // per distinct row: subbands whose lag differs from the previous row
     int* d_member_start = nullptr;
     int* d_member_ord = nullptr;
     int* d_ord2d = nullptr;
@@ -143,7 +144,7 @@ void free_all(lpf_stream* s) {
     if (!s) return;
     cudaSetDevice(s->dev);
     if (s->st) cudaStreamSynchronize(s->st);
-    void* ptrs[] = {s->ring, s->D, s->stage, s->d_lag, s->d_member_start, s->d_member_ord,
+    void* ptrs[] = {s->ring, s->D, s->stage, s->d_lag, s->d_chg, s->d_member_start, s->d_member_ord,
                     s->d_ord2d, s->d_dmax, s->keys[0], s->keys[1], s->vals[0], s->vals[1],
                     s->d_counter, s->d_hist, s->d_partials, s->d_yx};
     for (void* p : ptrs)
@@ -248,11 +249,14 @@ void launch_ingest(lpf_stream* s, const float* frame, int64_t slot) {
 
 template <typename TS>
 void launch_dedisperse(lpf_stream* s, int n_rows, int Tmod) {
-    const int rpb = 8;
-    dim3 grid((unsigned)((s->P / 4 + 255) / 256), (unsigned)((n_rows + rpb - 1) / rpb));
-    size_t smem = (size_t)rpb * s->F * sizeof(int64_t);
-    lpf::k_dedisperse<TS><<<grid, 256, smem, s->st>>>(reinterpret_cast<const TS*>(s->ring), s->D,
-                                                      s->d_lag, s->F, s->depth, Tmod, n_rows, rpb, s->P);
+    dim3 grid((unsigned)((s->P / 4 + 255) / 256));
+    const TS* ring = reinterpret_cast<const TS*>(s->ring);
+    if (s->F <= 8)
+        lpf::k_dedisperse<8, TS><<<grid, 256, 0, s->st>>>(ring, s->D, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, s->P);
+    else if (s->F <= 16)
+        lpf::k_dedisperse<16, TS><<<grid, 256, 0, s->st>>>(ring, s->D, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, s->P);
+    else
+        lpf::k_dedisperse<32, TS><<<grid, 256, 0, s->st>>>(ring, s->D, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, s->P);
 }
 
 template <typename TS>
@@ -431,7 +435,7 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
     if (params) prm = *params;
     if (H <= 0 || W <= 0 || F <= 0 || n_dm <= 0 || !freqs_mhz || !dm_grid || buffer_depth <= 0)
         return LPF_E_ARG;
-    if (H > (1 << 16) || W > (1 << 16) || buffer_depth > 32767) return LPF_E_ARG;
+    if (H > (1 << 16) || W > (1 << 16) || buffer_depth > 32767 || F > 32) return LPF_E_ARG;
     if (!(prm.cadence_s > 0) || prm.box_r < 1 || prm.box_r > 16 || prm.lmax_r != 1) return LPF_E_ARG;
     if (prm.dtype < LPF_FP32 || prm.dtype > LPF_BF16 || prm.cand_cap < 1 || prm.dyn_box_r < 0) return LPF_E_ARG;
     if (prm.result_slots < 1 || prm.result_slots > kMaxSlots) return LPF_E_ARG;
@@ -501,6 +505,7 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
     if (rc == LPF_OK) rc = dev_alloc(s, &s->D, (size_t)s->n_distinct * s->P);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->stage, (size_t)F * s->HW);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_lag, (size_t)s->n_distinct * F);
+    if (rc == LPF_OK) rc = dev_alloc(s, &s->d_chg, (size_t)s->n_distinct);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_member_start, s->member_start.size());
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_member_ord, s->member_ord.size());
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_ord2d, (size_t)n_dm);
@@ -535,8 +540,13 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
             for (int f = 0; f < F; ++f)
                 lag[(size_t)rr * F + f] = (int16_t)(s->dmax[d] - s->delay[(size_t)d * F + f]);
         }
+        std::vector<uint32_t> chg(s->n_distinct, 0);
+        for (int rr = 0; rr < s->n_distinct; ++rr)
+            for (int f = 0; f < F; ++f)
+                if (rr == 0 || lag[(size_t)rr * F + f] != lag[(size_t)(rr - 1) * F + f]) chg[rr] |= 1u << f;
         std::vector<int> dm32(s->dmax.begin(), s->dmax.end());
         if (cudaMemcpy(s->d_lag, lag.data(), lag.size() * sizeof(int16_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(s->d_chg, chg.data(), chg.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(s->d_member_start, s->member_start.data(), s->member_start.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(s->d_member_ord, s->member_ord.data(), s->member_ord.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(s->d_ord2d, s->ord2d.data(), s->ord2d.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
