@@ -53,6 +53,7 @@ extern "C" {
 #define LPF_E_CUDA       -9   /* a CUDA runtime call failed (no device, launch failure)  */
 #define LPF_E_BUSY      -10   /* all result slots hold unpolled frames; poll first       */
 #define LPF_E_NODATA    -11   /* poll with no pushed-and-unpolled frame                  */
+#define LPF_E_CAPACITY  -12   /* request larger than a fixed-capacity staging area       */
 
 /* storage type of the ring buffer (arithmetic is always FP32) */
 #define LPF_FP32 0
@@ -156,6 +157,37 @@ int lpf_poll_candidates(lpf_stream* s, lpf_candidate* out_host, int cap, int* n_
  */
 int lpf_extract_dynspec(lpf_stream* s, const lpf_candidate* c_host, int n, int Tw,
                         float* out_dev);
+
+/*
+ * lpf_extract_dynspec_static: the same gather as lpf_extract_dynspec, with the
+ * same arguments, results and errors, for callers that must not allocate
+ * device memory while they run.  The paper has no counterpart: this is a
+ * deployment variant, not a step of the method.
+ *
+ * Who needs it: lpf_extract_dynspec copies the candidate list into a device
+ * buffer that it enlarges with cudaMalloc when a call brings more candidates
+ * than any earlier call.  cudaMalloc can block on the whole device and take an
+ * unbounded time, and it spends memory outside any budget the caller keeps.
+ * A real-time loop that must meet a frame deadline, a server that admits
+ * streams against a fixed HBM budget, or a plug-in whose host application owns
+ * all device memory cannot have that happen inside a call.  This variant
+ * stages the records in a fixed array in device global memory instead and
+ * calls no allocating routine (no cudaMalloc, cudaFree or library allocator).
+ *
+ * Limits and sharing: at most LPF_STATIC_DYNSPEC_MAX candidates per call
+ * (LPF_E_CAPACITY above that).  The array (LPF_STATIC_DYNSPEC_MAX records of
+ * 24 bytes, 1.5 MiB) is part of the library image: every GPU that loads the
+ * library holds it until the process exits.  All calls on a device share it,
+ * so calls that overlap on the GPU race; issue them one at a time (from any
+ * handle or thread).  Each call writes the records it reads and synchronises
+ * the stream before returning, so nothing carries over between calls and the
+ * next call may start as soon as this one returns.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture.
+ */
+#define LPF_STATIC_DYNSPEC_MAX 65536
+int lpf_extract_dynspec_static(lpf_stream* s, const lpf_candidate* c_host, int n, int Tw,
+                               float* out_dev);
 
 /* Copy the integer delay table [n_dm][F] (frames) into out (HOST). */
 int lpf_get_delay_table(const lpf_stream* s, int32_t* out);

@@ -21,7 +21,8 @@ LIB_PATH = os.path.join(HERE, "liblpf.so")
 LPF_OK = 0
 LPF_E_ARG, LPF_E_DEPTH, LPF_E_ORDER, LPF_E_OOM, LPF_E_BUDGET = -1, -2, -3, -4, -5
 LPF_E_TRUNCATED, LPF_E_STALE, LPF_E_TIMEOUT, LPF_E_CUDA = -6, -7, -8, -9
-LPF_E_BUSY, LPF_E_NODATA = -10, -11
+LPF_E_BUSY, LPF_E_NODATA, LPF_E_CAPACITY = -10, -11, -12
+LPF_STATIC_DYNSPEC_MAX = 65536      # records accepted by lpf_extract_dynspec_static
 DTYPES = {"fp32": 0, "fp16": 1, "bf16": 2}
 
 # Every exported symbol declared in include/lpf.h (checked by the CPU tests).
@@ -29,7 +30,7 @@ EXPORTS = [
     "lpf_default_params", "lpf_stream_open", "lpf_push_frame", "lpf_push_frame_host",
     "lpf_poll_candidates", "lpf_extract_dynspec", "lpf_get_delay_table", "lpf_get_stats",
     "lpf_stream_info", "lpf_stream_sync", "lpf_stream_close", "lpf_strerror",
-    "lpf_set_profiling", "lpf_get_kernel_times",
+    "lpf_set_profiling", "lpf_get_kernel_times", "lpf_extract_dynspec_static",
 ]
 
 

@@ -16,6 +16,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <thread>
@@ -422,6 +423,7 @@ const char* lpf_strerror(int code) {
         case LPF_E_CUDA: return "CUDA error";
         case LPF_E_BUSY: return "all result slots are unpolled";
         case LPF_E_NODATA: return "no frame to poll";
+        case LPF_E_CAPACITY: return "request exceeds the fixed staging capacity";
         default: return "unknown error";
     }
 }
@@ -725,3 +727,114 @@ int lpf_get_kernel_times(lpf_stream* s, const char** names, double* total_ms, in
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Dynamic-spectrum gather for callers that cannot allocate device memory.
+//
+// lpf_extract_dynspec copies the caller's candidate list to a device buffer
+// that it grows with cudaMalloc when a call brings more candidates than any
+// earlier one.  This variant stages the candidate records in a fixed array in
+// device global memory instead, declared at file scope below, so the call
+// itself allocates nothing.  The array (LPF_STATIC_DYNSPEC_MAX records of 24
+// bytes, 1.5 MiB) exists on every GPU that loads the library, until exit.
+namespace {
+
+static_assert(sizeof(lpf::CandidateRec) == sizeof(lpf_candidate), "record layouts differ");
+
+static __device__ __align__(256) lpf::CandidateRec g_dynspec_records[LPF_STATIC_DYNSPEC_MAX];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_records_mu;
+lpf::CandidateRec* g_records_ptr[kMaxDevices] = {};
+
+// Device address of g_dynspec_records on the current device `dev`.  In host
+// code the array's name is only a host-side stand-in, so the address is looked
+// up once per device (cudaGetSymbolAddress, with that device current) and kept.
+int records_on_device(int dev, lpf::CandidateRec** out) {
+    if (dev < 0 || dev >= kMaxDevices) return LPF_E_CUDA;
+    std::lock_guard<std::mutex> lock(g_records_mu);
+    if (!g_records_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_dynspec_records) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return LPF_E_CUDA;
+        }
+        g_records_ptr[dev] = static_cast<lpf::CandidateRec*>(p);
+    }
+    *out = g_records_ptr[dev];
+    return LPF_OK;
+}
+
+// Same gather as lpf::k_dynspec, reading each pixel from a candidate record.
+template <typename TS>
+__global__ void k_dynspec_records(const TS* __restrict__ ring, const lpf::CandidateRec* __restrict__ c,
+                                  int n, int F, int Tw, int depth, int slot_first, int64_t P, int H,
+                                  int W, int box_r, float* __restrict__ out) {
+    const int64_t total = (int64_t)n * F * Tw;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int tau = (int)(idx % Tw);
+        int64_t rest = idx / Tw;
+        int f = (int)(rest % F);
+        int i = (int)(rest / F);
+        int slot = slot_first + tau;
+        if (slot >= depth) slot -= depth;
+        const TS* plane = ring + ((int64_t)slot * F + f) * P;
+        const int y = c[i].y, x = c[i].x;
+        float v;
+        if (box_r == 0) {
+            v = lpf::ld1(plane + (int64_t)y * W + x);
+        } else {
+            v = -INFINITY;
+            int ylo = max(y - box_r, 0), yhi = min(y + box_r, H - 1);
+            int xlo = max(x - box_r, 0), xhi = min(x + box_r, W - 1);
+            for (int yy = ylo; yy <= yhi; ++yy)
+                for (int xx = xlo; xx <= xhi; ++xx) v = fmaxf(v, lpf::ld1(plane + (int64_t)yy * W + xx));
+        }
+        out[idx] = v;
+    }
+}
+
+template <typename TS>
+void launch_dynspec_records(lpf_stream* s, const lpf::CandidateRec* rec, int n, int Tw, int slot_first,
+                            float* out) {
+    int64_t total = (int64_t)n * s->F * Tw;
+    int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 32);
+    if (blocks < 1) blocks = 1;
+    k_dynspec_records<TS><<<blocks, 256, 0, s->st>>>(reinterpret_cast<const TS*>(s->ring), rec, n, s->F, Tw,
+                                                     s->depth, slot_first, s->P, s->H, s->W,
+                                                     s->prm.dyn_box_r, out);
+}
+
+}  // namespace
+
+extern "C" int lpf_extract_dynspec_static(lpf_stream* s, const lpf_candidate* c_host, int n, int Tw,
+                                          float* out_dev) {
+    if (!s || n < 0 || Tw < 1 || (n > 0 && (!c_host || !out_dev))) return LPF_E_ARG;
+    if (n > LPF_STATIC_DYNSPEC_MAX) return LPF_E_CAPACITY;
+    if (Tw > s->depth) return LPF_E_DEPTH;
+    if (!s->polled) return LPF_E_NODATA;
+    const int64_t T = s->polled_T;
+    if (T - Tw + 1 < s->T_first) return LPF_E_STALE;
+    if (s->last_T - s->depth + 1 > T - Tw + 1) return LPF_E_STALE;
+    for (int i = 0; i < n; ++i)
+        if (c_host[i].y < 0 || c_host[i].y >= s->H || c_host[i].x < 0 || c_host[i].x >= s->W) return LPF_E_ARG;
+    if (n == 0) return LPF_OK;
+    if (cudaSetDevice(s->dev) != cudaSuccess) return LPF_E_CUDA;
+    lpf::CandidateRec* rec = nullptr;
+    int rc = records_on_device(s->dev, &rec);
+    if (rc != LPF_OK) return rc;
+    // every call writes the records it reads: nothing carries over between calls
+    LPF_TRY(cudaMemcpyAsync(rec, c_host, (size_t)n * sizeof(lpf_candidate), cudaMemcpyHostToDevice, s->st));
+    const int slot_first = (int)((T - Tw + 1) % s->depth);
+    cudaGetLastError();
+    switch (s->prm.dtype) {
+        case LPF_FP32: launch_dynspec_records<float>(s, rec, n, Tw, slot_first, out_dev); break;
+        case LPF_FP16: launch_dynspec_records<__half>(s, rec, n, Tw, slot_first, out_dev); break;
+        default: launch_dynspec_records<__nv_bfloat16>(s, rec, n, Tw, slot_first, out_dev); break;
+    }
+    if (cudaGetLastError() != cudaSuccess) return LPF_E_CUDA;
+    // the shared staging array is free for the next call once this returns
+    LPF_TRY(cudaStreamSynchronize(s->st));
+    return LPF_OK;
+}
