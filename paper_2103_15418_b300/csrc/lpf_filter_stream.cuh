@@ -104,6 +104,44 @@ __device__ __forceinline__ float2 row_count(int y, int H) {
     return make_float2((float)c, 1.0f / (float)c);
 }
 
+// Candidates of one image row of a warp (rare): 3x3 local maximum of D clipped
+// to the image (ties count as maxima), then one warp-aggregated reservation and
+// one record per DM trial sharing this delay row.  Kept out of line so the
+// unrolled row loops stay small.  Every lane of the warp calls it.
+__device__ __noinline__ void emit_candidates(const FilterArgs& a, const float* Dimg, int ys, int xc,
+                                             float snr, bool cand, int m0, int nm) {
+    const int H = a.H, W = a.W;
+    const int lane = threadIdx.x & 31;
+    if (cand) {
+        const float* p = Dimg + (int64_t)ys * W + xc;
+        const float dv = __ldg(p);
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (dy == 0 && dx == 0) continue;
+                int yy = ys + dy, xx = xc + dx;
+                if (yy >= 0 && yy < H && xx >= 0 && xx < W && __ldg(p + (int64_t)dy * W + dx) > dv)
+                    cand = false;
+            }
+    }
+    unsigned bal = __ballot_sync(0xffffffffu, cand);
+    if (!bal) return;
+    int leader = __ffs(bal) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(a.counter, (unsigned)(__popc(bal) * nm));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (cand) {
+        unsigned rank = __popc(bal & ((1u << lane) - 1u));
+        uint64_t pix = ((uint64_t)ys << a.bx) | (uint64_t)xc;
+        for (int m = 0; m < nm; ++m) {
+            unsigned idx = base + rank * nm + m;
+            if (idx < (unsigned)a.cap) {
+                a.keys[idx] = ((uint64_t)a.member_ord[m0 + m] << (a.bx + a.by)) | pix;
+                a.vals[idx] = snr;
+            }
+        }
+    }
+}
+
 template <int R>
 __global__ void __launch_bounds__(kStreamThreads, 2) k_filter_stream(FilterArgs a) {
     using G = StreamGeom<R>;
@@ -219,41 +257,9 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_filter_stream(FilterArgs 
                     s2 = fmaf(snr, snr, s2);
                     cnt += 1.f;
                 }
-                bool cand = valid && snr > a.kappa;
-                if (__any_sync(0xffffffffu, cand)) {
-                    if (cand) {
-                        const float* p = Dimg + (int64_t)ys * W + xc;
-                        const float dv = __ldg(p);
-#pragma unroll
-                        for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-                            for (int dx = -1; dx <= 1; ++dx) {
-                                if (dy == 0 && dx == 0) continue;
-                                int yy = ys + dy, xx = xc + dx;
-                                if (yy >= 0 && yy < H && xx >= 0 && xx < W &&
-                                    __ldg(p + (int64_t)dy * W + dx) > dv)
-                                    cand = false;
-                            }
-                    }
-                    unsigned bal = __ballot_sync(0xffffffffu, cand);
-                    if (bal) {
-                        int leader = __ffs(bal) - 1;
-                        unsigned base = 0;
-                        if (lane == leader) base = atomicAdd(a.counter, (unsigned)(__popc(bal) * nm));
-                        base = __shfl_sync(0xffffffffu, base, leader);
-                        if (cand) {
-                            unsigned rank = __popc(bal & ((1u << lane) - 1u));
-                            uint64_t pix = ((uint64_t)ys << a.bx) | (uint64_t)xc;
-                            for (int m = 0; m < nm; ++m) {
-                                unsigned idx = base + rank * nm + m;
-                                if (idx < (unsigned)a.cap) {
-                                    a.keys[idx] = ((uint64_t)a.member_ord[m0 + m] << (a.bx + a.by)) | pix;
-                                    a.vals[idx] = snr;
-                                }
-                            }
-                        }
-                    }
-                }
+                const bool cand = valid && snr > a.kappa;
+                if (__any_sync(0xffffffffu, cand))
+                    emit_candidates(a, Dimg, ys, xc, snr, cand, m0, nm);
             }
             d1 += s1;
             d2 += s2;
