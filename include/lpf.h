@@ -116,6 +116,15 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
                     int n_dm, const double* dm_grid, int buffer_depth, const lpf_params* params);
 
 /*
+ * Device bytes lpf_stream_open would request for these arguments, computed on
+ * the host without any CUDA call (the same validation and errors as open).
+ * The allocator may round each of the stream's ~20 allocations up.
+ */
+int lpf_stream_footprint(int H, int W, int F, const double* freqs_mhz, int n_dm,
+                         const double* dm_grid, int buffer_depth, const lpf_params* params,
+                         size_t* bytes);
+
+/*
  * Push frame T: frame_dev is a DEVICE pointer to F*H*W FP32 values laid out
  * [F][H][W] (row-major, subband-major), on the stream's device.  The work is
  * enqueued on the stream's CUDA stream and the call returns at once; the
@@ -218,6 +227,68 @@ const char* lpf_strerror(int code);
 int lpf_set_profiling(lpf_stream* s, int on);
 int lpf_get_kernel_times(lpf_stream* s, const char** names, double* total_ms,
                          int64_t* launches, int n, int reset);
+
+/* ------------------------------------------------------------------ serving
+ * A server multiplexes several concurrent streams (different sizes, subbands
+ * and DM grids) on the current CUDA device under an HBM budget.  A persistent
+ * worker thread owns every stream: it admits requested streams in request
+ * order as soon as their device footprint (lpf_stream_footprint) fits the
+ * budget left by the admitted ones, moves each stream's submitted frames onto
+ * the GPU whenever the stream has a free result slot, and collects finished
+ * frames without blocking.  Each stream runs on its own CUDA stream, so work
+ * of different streams overlaps on the device; the result of a stream does
+ * not depend on what else is being served.  All functions are thread-safe.
+ */
+typedef struct lpf_server lpf_server;
+
+#define LPF_SERVE_PENDING 0   /* requested, waiting for budget                     */
+#define LPF_SERVE_ACTIVE  1   /* admitted: ring buffer and scratch resident         */
+#define LPF_SERVE_CLOSED  3   /* drained and released (or failed to open)           */
+
+typedef struct {
+    int64_t frames;          /* frames finished                                      */
+    double  p50_ms, p99_ms, max_ms;   /* submit -> finished latency                  */
+    double  pixel_dm_per_s;  /* H*W*n_dm per finished frame / (first submit -> last finish) */
+    size_t  budget_bytes, used_bytes;
+} lpf_serve_stats_t;
+
+/* Start a server with an HBM budget (bytes) for its streams' device memory and
+ * at most max_streams live (pending or admitted) streams.  Errors: LPF_E_ARG,
+ * LPF_E_CUDA (no device), LPF_E_OOM. */
+int lpf_server_open(lpf_server** out, size_t hbm_budget_bytes, int max_streams);
+
+/* Request a stream (arguments as lpf_stream_open; params->cuda_stream is
+ * ignored).  Returns its id at once; it is admitted when its footprint fits.
+ * Frames may be submitted before admission; they queue.  Errors: those of
+ * lpf_stream_footprint, LPF_E_BUDGET (larger than the whole budget),
+ * LPF_E_BUSY (max_streams live), LPF_E_OOM (pinned frame buffers). */
+int lpf_server_open_stream(lpf_server* srv, int H, int W, int F, const double* freqs_mhz,
+                           int n_dm, const double* dm_grid, int buffer_depth,
+                           const lpf_params* params, int* id_out);
+
+/* Submit frame T ([F][H][W] FP32, HOST) of stream id; copied into the
+ * stream's pinned buffers before returning.  Frames of a stream must be
+ * submitted in consecutive order.  LPF_E_BUSY when result_slots + 4 frames
+ * of the stream are queued or in flight (fetch, then retry). */
+int lpf_server_submit(lpf_server* srv, int id, const float* frame_host, int64_t T);
+
+/* Next finished frame of stream id, in submission order: candidates (as
+ * lpf_poll_candidates), frame index and submit-to-finish latency.  Waits up
+ * to timeout_ms (< 0: until finished or the stream closed).  LPF_E_TIMEOUT,
+ * LPF_E_NODATA (stream closed and drained), or the frame's own error code. */
+int lpf_server_fetch(lpf_server* srv, int id, lpf_candidate* out_host, int cap, int* n_out,
+                     int64_t* T_out, double* latency_ms, int timeout_ms);
+
+/* Close stream id after its queued frames finish; its budget then admits
+ * waiting streams.  Unfetched results stay fetchable. */
+int lpf_server_close_stream(lpf_server* srv, int id);
+int lpf_server_stream_state(lpf_server* srv, int id, int* state);
+
+/* Latency and throughput of stream id, or of all streams (id = -1). */
+int lpf_server_stats(lpf_server* srv, int id, lpf_serve_stats_t* out);
+
+/* Stop the worker, wait for all device work and release every stream. */
+int lpf_server_close(lpf_server* srv);
 
 #ifdef __cplusplus
 }

@@ -31,7 +31,11 @@ EXPORTS = [
     "lpf_poll_candidates", "lpf_extract_dynspec", "lpf_get_delay_table", "lpf_get_stats",
     "lpf_stream_info", "lpf_stream_sync", "lpf_stream_close", "lpf_strerror",
     "lpf_set_profiling", "lpf_get_kernel_times", "lpf_extract_dynspec_static",
+    "lpf_stream_footprint", "lpf_server_open", "lpf_server_open_stream", "lpf_server_submit",
+    "lpf_server_fetch", "lpf_server_close_stream", "lpf_server_stream_state", "lpf_server_stats",
+    "lpf_server_close",
 ]
+SERVE_PENDING, SERVE_ACTIVE, SERVE_CLOSED = 0, 1, 3
 
 
 class Params(Structure):
@@ -43,6 +47,11 @@ class Params(Structure):
 class Candidate(Structure):
     _fields_ = [("t0", c_int64), ("dm_idx", c_int32), ("y", c_int32), ("x", c_int32),
                 ("snr", c_float)]
+
+
+class ServeStats(Structure):
+    _fields_ = [("frames", c_int64), ("p50_ms", c_double), ("p99_ms", c_double), ("max_ms", c_double),
+                ("pixel_dm_per_s", c_double), ("budget_bytes", c_size_t), ("used_bytes", c_size_t)]
 
 
 class StreamInfo(Structure):
@@ -94,6 +103,18 @@ def load(path: Optional[str] = None):
     lib.lpf_set_profiling.argtypes = [c_void_p, c_int]
     lib.lpf_get_kernel_times.argtypes = [c_void_p, POINTER(c_char_p), POINTER(c_double),
                                          POINTER(c_int64), c_int, c_int]
+    lib.lpf_stream_footprint.argtypes = [c_int, c_int, c_int, POINTER(c_double), c_int, POINTER(c_double),
+                                         c_int, POINTER(Params), POINTER(c_size_t)]
+    lib.lpf_server_open.argtypes = [POINTER(c_void_p), c_size_t, c_int]
+    lib.lpf_server_open_stream.argtypes = [c_void_p, c_int, c_int, c_int, POINTER(c_double), c_int,
+                                           POINTER(c_double), c_int, POINTER(Params), POINTER(c_int)]
+    lib.lpf_server_submit.argtypes = [c_void_p, c_int, c_void_p, c_int64]
+    lib.lpf_server_fetch.argtypes = [c_void_p, c_int, c_void_p, c_int, POINTER(c_int), POINTER(c_int64),
+                                     POINTER(c_double), c_int]
+    lib.lpf_server_close_stream.argtypes = [c_void_p, c_int]
+    lib.lpf_server_stream_state.argtypes = [c_void_p, c_int, POINTER(c_int)]
+    lib.lpf_server_stats.argtypes = [c_void_p, c_int, POINTER(ServeStats)]
+    lib.lpf_server_close.argtypes = [c_void_p]
     _lib = lib
     return lib
 
@@ -101,6 +122,28 @@ def load(path: Optional[str] = None):
 def _check(rc: int, what: str):
     if rc != LPF_OK:
         raise LpfError(rc, what)
+
+
+def make_params(*, cadence_s: float = 1.0, kappa: float = 6.0, box_r: int = 15, dtype: str = "fp32",
+                cand_cap: int = 1 << 20, dyn_box_r: int = 0, result_slots: int = 2,
+                filter_impl: str = "auto") -> "Params":
+    p = default_params()
+    p.cadence_s, p.kappa, p.box_r = cadence_s, kappa, box_r
+    p.dtype, p.cand_cap, p.dyn_box_r, p.result_slots = DTYPES[dtype], cand_cap, dyn_box_r, result_slots
+    p.filter_impl = {"auto": 0, "tiled": 1, "streaming": 2}[filter_impl]
+    return p
+
+
+def footprint(H: int, W: int, freqs_mhz, dm_grid, depth: int, **kw) -> int:
+    """Device bytes a stream with these arguments allocates (host-side plan, no GPU)."""
+    f = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
+    d = np.ascontiguousarray(dm_grid, dtype=np.float64)
+    p = make_params(**kw)
+    out = c_size_t(0)
+    _check(load().lpf_stream_footprint(int(H), int(W), len(f), f.ctypes.data_as(POINTER(c_double)), len(d),
+                                       d.ctypes.data_as(POINTER(c_double)), int(depth), ctypes.byref(p),
+                                       ctypes.byref(out)), "lpf_stream_footprint")
+    return int(out.value)
 
 
 def default_params() -> Params:
@@ -214,6 +257,80 @@ class Stream:
     def close(self) -> None:
         if getattr(self, "_h", None):
             load().lpf_stream_close(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving loop: concurrent streams on one GPU under an HBM budget (C++ worker thread)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_streams: int = 16):
+        h = c_void_p()
+        _check(load().lpf_server_open(ctypes.byref(h), int(hbm_budget_bytes), int(max_streams)),
+               "lpf_server_open")
+        self._h = h
+        self._meta = {}
+
+    def open_stream(self, H: int, W: int, freqs_mhz, dm_grid, depth: int, **kw) -> int:
+        f = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
+        d = np.ascontiguousarray(dm_grid, dtype=np.float64)
+        p = make_params(**kw)
+        sid = c_int(-1)
+        _check(load().lpf_server_open_stream(self._h, int(H), int(W), len(f),
+                                             f.ctypes.data_as(POINTER(c_double)), len(d),
+                                             d.ctypes.data_as(POINTER(c_double)), int(depth),
+                                             ctypes.byref(p), ctypes.byref(sid)), "lpf_server_open_stream")
+        self._meta[sid.value] = (len(f), int(H), int(W), int(p.cand_cap))
+        return sid.value
+
+    def submit(self, sid: int, frame: np.ndarray, T: int) -> int:
+        """Returns LPF_OK or LPF_E_BUSY (retry after a fetch); raises on other errors."""
+        fr = np.ascontiguousarray(frame, dtype=np.float32)
+        rc = load().lpf_server_submit(self._h, int(sid), c_void_p(fr.ctypes.data), int(T))
+        if rc not in (LPF_OK, LPF_E_BUSY):
+            raise LpfError(rc, "lpf_server_submit")
+        return rc
+
+    def fetch(self, sid: int, timeout_ms: int = -1):
+        """(T, candidates, n_found, latency_ms) of the stream's next finished frame."""
+        cap = self._meta[sid][3]
+        buf = np.zeros(cap, dtype=CANDIDATE_DTYPE)
+        n = c_int(0)
+        T = c_int64(-1)
+        lat = c_double(0.0)
+        rc = load().lpf_server_fetch(self._h, int(sid), c_void_p(buf.ctypes.data), cap, ctypes.byref(n),
+                                     ctypes.byref(T), ctypes.byref(lat), int(timeout_ms))
+        if rc not in (LPF_OK, LPF_E_TRUNCATED):
+            raise LpfError(rc, "lpf_server_fetch")
+        return T.value, buf[:min(n.value, cap)].copy(), n.value, lat.value
+
+    def close_stream(self, sid: int) -> None:
+        _check(load().lpf_server_close_stream(self._h, int(sid)), "lpf_server_close_stream")
+
+    def state(self, sid: int) -> int:
+        st = c_int(-1)
+        _check(load().lpf_server_stream_state(self._h, int(sid), ctypes.byref(st)), "lpf_server_stream_state")
+        return st.value
+
+    def stats(self, sid: int = -1) -> Dict[str, float]:
+        o = ServeStats()
+        _check(load().lpf_server_stats(self._h, int(sid), ctypes.byref(o)), "lpf_server_stats")
+        return {k: getattr(o, k) for k, _ in ServeStats._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().lpf_server_close(self._h)
             self._h = None
 
     def __enter__(self):

@@ -388,27 +388,47 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint64_t* __rest
     hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of hist[256 * nb] (digit-major) in one block of 1024 threads
-__global__ void __launch_bounds__(1024) k_rs_scan(unsigned* __restrict__ hist, int total) {
-    __shared__ unsigned part[1024];
-    const int per = (total + 1023) / 1024;
-    const int lo = threadIdx.x * per, hi = min(total, lo + per);
-    unsigned s = 0;
-    for (int i = lo; i < hi; ++i) s += hist[i];
-    part[threadIdx.x] = s;
+// Exclusive scan of hist[256 * nb] in digit-major order, one block of 1024
+// threads: each warp scans the nb block counts of 8 digits with coalesced loads
+// and warp shuffles, then the 256 digit totals are scanned and added back.
+__global__ void __launch_bounds__(1024) k_rs_scan(unsigned* __restrict__ hist, int nb) {
+    __shared__ unsigned tot[256];
+    __shared__ unsigned base[256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = warp; d < 256; d += 32) {
+        unsigned run = 0;
+        for (int c = 0; c < nb; c += 32) {
+            int i = c + lane;
+            unsigned v = i < nb ? hist[d * nb + i] : 0u;
+            unsigned inc = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned u = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += u;
+            }
+            if (i < nb) hist[d * nb + i] = run + inc - v;
+            run += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        if (lane == 0) tot[d] = run;
+    }
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        unsigned v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
+    if (warp == 0) {
+        unsigned v[8], s = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { v[k] = tot[lane * 8 + k]; s += v[k]; }
+        unsigned inc = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        unsigned run = inc - s;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { base[lane * 8 + k] = run; run += v[k]; }
     }
-    unsigned run = part[threadIdx.x] - s;
-    for (int i = lo; i < hi; ++i) {
-        unsigned v = hist[i];
-        hist[i] = run;
-        run += v;
-    }
+    __syncthreads();
+    for (int d = warp; d < 256; d += 32)
+        for (int i = lane; i < nb; i += 32) hist[d * nb + i] += base[d];
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(

@@ -351,7 +351,7 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
     for (int shift = 0; shift < s->key_bits; shift += 8) {
         lpf::k_rs_hist<<<kSortBlocks, lpf::kSortThreads, 0, s->st>>>(s->keys[cur], s->d_counter,
                                                                        s->prm.cand_cap, shift, s->d_hist);
-        lpf::k_rs_scan<<<1, 1024, 0, s->st>>>(s->d_hist, 256 * kSortBlocks);
+        lpf::k_rs_scan<<<1, 1024, 0, s->st>>>(s->d_hist, kSortBlocks);
         lpf::k_rs_scatter<<<kSortBlocks, lpf::kSortThreads, 0, s->st>>>(
             s->keys[cur], s->vals[cur], s->keys[cur ^ 1], s->vals[cur ^ 1], s->d_counter,
             s->prm.cand_cap, shift, s->d_hist);
@@ -428,9 +428,14 @@ const char* lpf_strerror(int code) {
     }
 }
 
-int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, int n_dm,
-                    const double* dm_grid, int buffer_depth, const lpf_params* params) {
-    if (!out) return LPF_E_ARG;
+}  // extern "C"
+
+namespace {
+
+// Validate the arguments and build the host-side plan (delay table, distinct
+// rows, launch geometry) of a stream; no CUDA call.
+int plan_stream(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, int n_dm,
+                const double* dm_grid, int buffer_depth, const lpf_params* params) {
     *out = nullptr;
     lpf_params prm;
     lpf_default_params(&prm);
@@ -478,6 +483,49 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
     s->n_strips = (W + lpf::kStreamTX - 1) / lpf::kStreamTX;
     if (s->stream_filter)
         s->filter_smem = (prm.box_r == 7 ? lpf::StreamGeom<7>::smem_floats : lpf::StreamGeom<15>::smem_floats) * sizeof(float);
+    *out = s;
+    return LPF_OK;
+}
+
+// Device bytes lpf_stream_open requests for a planned stream (the sum of the
+// allocation sizes; the allocator may round each one up).
+size_t footprint_bytes(const lpf_stream* s) {
+    auto b = [](size_t n) { return std::max<size_t>(n, 16); };
+    const size_t nd = (size_t)s->n_distinct, cap = (size_t)s->prm.cand_cap;
+    size_t t = (size_t)s->depth * s->F * s->P * s->elem;
+    t += b(nd * s->P * 4) + b((size_t)s->F * s->HW * 4) + b(nd * s->F * 2) + b(nd * 4);
+    t += b(s->member_start.size() * 4) + b(s->member_ord.size() * 4) + 2 * b((size_t)s->n_dm * 4);
+    t += 2 * (b(cap * 8) + b(cap * 4)) + b(16) + b((size_t)256 * kSortBlocks * 4);
+    t += b(nd * n_filter_blocks(s) * 3 * 8);
+    t += (size_t)s->n_slots * (b(cap * sizeof(lpf::CandidateRec)) + b(nd * 3 * 8));
+    return t;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lpf_stream_footprint(int H, int W, int F, const double* freqs_mhz, int n_dm, const double* dm_grid,
+                         int buffer_depth, const lpf_params* params, size_t* bytes) {
+    if (!bytes) return LPF_E_ARG;
+    lpf_stream* s = nullptr;
+    int rc = plan_stream(&s, H, W, F, freqs_mhz, n_dm, dm_grid, buffer_depth, params);
+    if (rc != LPF_OK) return rc;
+    *bytes = footprint_bytes(s);
+    delete s;
+    return LPF_OK;
+}
+
+int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, int n_dm,
+                    const double* dm_grid, int buffer_depth, const lpf_params* params) {
+    if (!out) return LPF_E_ARG;
+    *out = nullptr;
+    lpf_stream* s = nullptr;
+    {
+        int prc = plan_stream(&s, H, W, F, freqs_mhz, n_dm, dm_grid, buffer_depth, params);
+        if (prc != LPF_OK) return prc;
+    }
+    const lpf_params prm = s->prm;
 
     int rc = LPF_OK;
     if (cudaGetDevice(&s->dev) != cudaSuccess) { cudaGetLastError(); delete s; return LPF_E_CUDA; }

@@ -235,7 +235,7 @@ def spec_stress(depth: int = 114, **kw) -> StreamSpec:
     """2048x2048 px, 32 subbands from 57.6 MHz, DM 0..500 step 0.5 (1001 trials), FP16."""
     d = dict(name="stress", H=2048, W=2048, freqs_mhz=subband_centres([57.6], 32),
              dm_grid=np.arange(1001, dtype=np.float64) * 0.5, depth=depth, n_frames=600,
-             box_r=15, kappa=6.0, gradient_amp=3.0, n_sources=300, source_flux=(5.0, 500.0),
+             box_r=15, kappa=6.0, gradient_amp=3.0, n_sources=0, source_flux=(5.0, 500.0),
              psf_sigma=1.5, n_pulses=200, pulse_dm=(5.0, 480.0), pulse_width=(1.0, 4.0),
              pulse_alpha=(-2.0, 2.0), pulse_peak=None, pulse_fluence=(6.0, 30.0),
              rfi_fraction=0.01, rfi_amp=10.0, dtype="fp16")

@@ -72,3 +72,30 @@ def test_null_handles_are_rejected():
     assert lib.lpf_push_frame(None, None, 0) == lpf.LPF_E_ARG
     assert lib.lpf_poll_candidates(None, None, 0, None, None, 0) == lpf.LPF_E_ARG
     assert lib.lpf_stream_close(None) == lpf.LPF_OK
+
+
+def test_footprint_is_planned_without_a_gpu():
+    import synth
+    sp = synth.spec_aartfaac()
+    fp32 = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth)
+    fp16 = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth, dtype="fp16")
+    ring32 = sp.depth * sp.F * sp.H * sp.W * 4
+    # ring + 205 dedispersed images + candidate buffers
+    assert ring32 + 205 * sp.H * sp.W * 4 < fp32 < ring32 + 205 * sp.H * sp.W * 4 + 400 * 2 ** 20
+    assert fp32 - fp16 == ring32 // 2
+    deeper = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth + 10)
+    assert deeper - fp32 == 10 * sp.F * sp.H * sp.W * 4
+    with pytest.raises(lpf.LpfError) as e:
+        lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, 40)
+    assert e.value.code == lpf.LPF_E_DEPTH
+
+
+def test_stress_config_depth_96_is_rejected():
+    """2048^2 x 32 subbands over 57.6-63.85 MHz, DM up to 500: the sweep needs 114 frames."""
+    import synth
+    sp = synth.spec_stress(depth=96)
+    with pytest.raises(lpf.LpfError) as e:
+        lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth, dtype="fp16")
+    assert e.value.code == lpf.LPF_E_DEPTH
+    fp = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, 114, dtype="fp16")
+    assert 40e9 < fp < 50e9        # 30.6 GB ring + 13.5 GB dedispersed images

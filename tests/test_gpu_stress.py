@@ -1,0 +1,44 @@
+"""Stress workload: 2048^2 px, 32 subbands (57.6-63.85 MHz), 1001 DM trials, FP16 ring.
+
+The sweep of DM 500 spans 113 frames, so the ring needs depth 114 (depth 96 is
+rejected, see test_abi_cpu).  12 synthetic frames (dispersed pulses, 1% RFI
+stripes) are cycled to fill the ring; the oracle reads the same cycle.  Checks
+sampled trials against the oracle and the 32 x 64 FP32 dynamic spectra of the
+frame's candidates against direct indexing of the frames.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import lpf_oracle as O
+from tests.parity import assert_sorted_unique, compare_push
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def test_stress_sampled_trials_and_dynspec(lib):
+    spec = synth.spec_stress(depth=114)
+    st = synth.SyntheticStream(spec, seed=50)
+    pool = [st.frame(t) for t in range(12)]
+    pool[5][:, 1000, :] += 10.0                      # one broadband RFI stripe in the cycle
+    frame_at = lambda t: O.storage_round(pool[t % 12], "fp16")
+    delays = O.delay_table(spec.freqs_mhz, spec.dm_grid, spec.cadence_s)
+    T = int(delays.max()) + 3
+    dev_pool = [torch.from_numpy(p).cuda() for p in pool]
+    with lib.Stream(spec.H, spec.W, spec.freqs_mhz, spec.dm_grid, spec.depth, kappa=spec.kappa,
+                    box_r=spec.box_r, dtype="fp16") as s:
+        for t in range(T + 1):
+            s.push(dev_pool[t % 12], t)
+            _, c, n, trunc = s.poll(timeout_ms=120000)
+        assert not trunc
+        assert_sorted_unique(c)
+        compare_push(c, frame_at, T, delays, spec.box_r, spec.kappa, dms=[0, 1, 400, 1000],
+                     gpu_stats=s.stats())
+        Tw = 64
+        ds = s.dynspec(c, Tw)                              # contiguous [n][32][64] FP32 batch
+        assert ds.shape == (len(c), 32, Tw) and ds.is_contiguous()
+        pick = np.linspace(0, len(c) - 1, min(len(c), 50)).astype(int) if len(c) else []
+        if len(c):
+            ref = O.dynspec(frame_at, T, Tw, [(int(c["y"][i]), int(c["x"][i])) for i in pick])
+            np.testing.assert_array_equal(ds.cpu().numpy()[pick], ref.astype(np.float32))
