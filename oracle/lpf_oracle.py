@@ -17,6 +17,9 @@ method, each citing the passage of Ruhe et al. (arXiv 2103.15418) it follows:
   detect           Sec. 2.1.2, p = q AND y
   frame_stats      mean / RMS of S/N over valid pixels (diagnostic noise level)
   dynspec          Sec. 2.2, flux measurement + backward fill from cached images
+  search_push_residual  the same search with D - C as a shift-sum of per-subband
+                   residuals X - C(X) (linearity of the local centre); reference
+                   for rings that store those residuals in reduced precision
 
 Readings where the paper is silent or garbled (all listed in the design doc):
   * C_DM = 4.148808e3 s MHz^2 cm^3 / pc (the printed unit "ms" is garbled; with
@@ -218,6 +221,46 @@ def search_push(frame_at: FrameFn, T: int, delays: np.ndarray, r: int, kappa: fl
             res["abs_sum"] = abs_sum(frame_at, T, delays, d)
             res["t0"] = t0
             maps[d] = res
+    cands.sort(key=lambda c: (c[0], c[1], c[2], c[3]))
+    return cands, stats, maps
+
+
+# --------------------------------------------------------------------- residual form
+def residual_frame(frame: np.ndarray, r: int) -> np.ndarray:
+    """X - C(X) for every subband plane of one frame (Sec. 2.1.1 local centre per plane)."""
+    frame = np.asarray(frame, dtype=np.float64)
+    return np.stack([frame[f] - local_centre(frame[f], r) for f in range(frame.shape[0])])
+
+
+def search_push_residual(raw_at: FrameFn, res_at: FrameFn, T: int, delays: np.ndarray, r: int,
+                         kappa: float, T_first: int = 0, dms: Optional[Sequence[int]] = None,
+                         keep_maps: bool = False):
+    """The search with D - C formed as the shift-sum of per-subband residuals.
+
+    The local centre is linear and the same clipped window serves every plane,
+    so D_d - C_d = sum_f (X_f - C(X_f)) at the shifted frames (Sec. 2.1.1,
+    App. B.2); S = box mean of (D - C)^2, snr = (D - C)/sqrt(S); the local
+    maximum is taken on D from raw_at.  With res_at = residual_frame(raw_at)
+    this equals search_push exactly (up to rounding order); a ring that stores
+    the residuals in reduced precision is reproduced by rounding res_at.
+    """
+    cands, stats, maps = [], {}, {}
+    for d in (active_trials(delays, T, T_first) if dms is None else dms):
+        t0, D = dedisperse(raw_at, T, delays, d)
+        _, Rd = dedisperse(res_at, T, delays, d)
+        S = box_sum(Rd * Rd, r) / window_count(*Rd.shape, r)
+        snr = np.zeros_like(Rd)
+        ok = S > 0
+        snr[ok] = Rd[ok] / np.sqrt(S[ok])
+        q = local_max_mask(D)
+        mask = (snr > kappa) & q & ok
+        ys, xs = np.nonzero(mask)
+        for y, x in zip(ys, xs):
+            cands.append((t0, d, int(y), int(x), float(snr[y, x])))
+        stats[d] = frame_stats(snr, ok)
+        if keep_maps:
+            maps[d] = dict(D=D, S=S, snr=snr, valid=ok, mask=mask, lmax_margin=D - neighbour_max(D),
+                           abs_sum=abs_sum(raw_at, T, delays, d), t0=t0)
     cands.sort(key=lambda c: (c[0], c[1], c[2], c[3]))
     return cands, stats, maps
 

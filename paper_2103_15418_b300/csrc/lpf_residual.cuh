@@ -1,0 +1,311 @@
+// Residual path: the box filter moved in front of the shift-sum.
+//
+// The local centre is linear in the image and the shift-sum only moves whole
+// planes in time, so for every DM trial d and pixel p (Sec. 2.1.1, App. B.2)
+//   C_d(p) = (1/n_p) sum_{q in W(p)} sum_f X_f(t_f)(q) = sum_f C(X_f(t_f))(p)
+//   D_d(p) - C_d(p) = sum_f [X_f(t_f) - C(X_f(t_f))](p) = sum_f Xr_f(t_f)(p),
+// with the same clipped window W(p) and count n_p for every plane.  So:
+//   k_residual   once per frame and subband: Xr = X - C(X) into a residual ring
+//   k_dedisperse over the residual ring gives R_d = D_d - C_d per distinct row
+//   k_filter_res S_d = box mean of R_d^2, snr = R_d / sqrt(S_d), threshold,
+//                3x3 local maximum of D_d (formed from the raw ring at the
+//                candidate pixels only), stats, emission.
+// One box filter per trial instead of two, with a halo of r instead of 2r.
+#pragma once
+#include "lpf_filter_stream.cuh"
+
+namespace lpf {
+
+template <int R>
+struct ResGeom {
+    static constexpr int TX = 128;
+    static constexpr int L = 2 * R + 1;
+    static constexpr int NP = 32 / L;
+    static constexpr int B = NP * L;                 // rows per block
+    static constexpr int WD = TX + 2 * R;             // columns carrying the input of one box pass
+    static constexpr int SD = WD | 1;
+    static constexpr int SX = TX | 1;
+    static constexpr int NR = (TX + L - 1) / L;       // horizontal runs per row
+    static constexpr int RR = (TX + NR - 1) / NR;
+    static constexpr int NT = 160;
+    static_assert(WD <= NT, "one thread per loaded column");
+};
+
+// ---------------------------------------------------------------------------
+// k_residual: Xr = X - C(X) for the F planes of one ring slot, C the clipped box
+// mean of radius R (horizontal two-stack sums, vertical sliding sum, C by
+// reciprocal plus one Newton step against the exact count, so a constant
+// window gives Xr = 0 exactly).  X is read as stored (storage type TS) and Xr
+// is written in the storage type.  Grid: (strips, F).
+template <int R, typename TS>
+__global__ void __launch_bounds__(ResGeom<R>::NT) k_residual(const TS* __restrict__ raw_slot,
+                                                             TS* __restrict__ res_slot, int H, int W,
+                                                             int64_t P) {
+    using G = ResGeom<R>;
+    constexpr int TX = G::TX, B = G::B, L = G::L, SD = G::SD, SX = G::SX, WD = G::WD;
+    extern __shared__ float smr[];
+    float(*Xb)[B][SD] = reinterpret_cast<float(*)[B][SD]>(smr);        // [2][B][SD] this and the previous block
+    float(*hX)[SX] = reinterpret_cast<float(*)[SX]>(smr + 2 * B * SD);  // [B][SX]
+    __shared__ float2 rowC[B];
+    const int strip = blockIdx.x, f = blockIdx.y;
+    const int x0 = strip * TX;
+    const TS* X = raw_slot + (int64_t)f * P;
+    TS* Xr = res_slot + (int64_t)f * P;
+    const int t = threadIdx.x;
+    const int xl = x0 - R + t;                  // loaded column of this thread
+    const bool lcol = t < WD && xl >= 0 && xl < W;
+    const int xs = x0 + t;                      // output column of this thread
+    const bool ocol = t < TX && xs < W;
+    const int nx = ocol ? min(xs + R, W - 1) - max(xs - R, 0) + 1 : 0;
+    const float nxf = (float)nx, inv_nx = ocol ? 1.0f / nxf : 0.f;
+    float hist[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) hist[i] = 0.f;
+    float v = 0.f;
+    const int nblk = (H + R + B - 1) / B;
+    for (int k = 0; k < nblk; ++k) {
+        const int ybase = k * B;
+        float(*cur)[SD] = Xb[k & 1];
+        float(*prev)[SD] = Xb[(k + 1) & 1];
+        if (t < WD) {
+            const TS* src = X + (int64_t)ybase * W + xl;
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                cur[j][t] = (lcol && ybase + j < H) ? ld1(src) : 0.f;
+                src += W;
+            }
+        }
+        if (t < B) rowC[t] = row_count<R>(ybase + t - R, H);
+        __syncthreads();
+        for (int it = t; it < B * G::NR; it += G::NT) {
+            int j = it % B, run = it / B;
+            int c0 = run * G::RR;
+            int len = min(G::RR, TX - c0);
+            const float* in = cur[j];
+            float* out = hX[j];
+            two_stack_run<R, G::RR>(c0, len, [&](int c) { return in[c]; },
+                                    [&](int c, float val) { out[c] = val; });
+        }
+        __syncthreads();
+        if (t < TX) {
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                float in = hX[j][t];
+                float out = hist[j % L];
+                hist[j % L] = in;
+                v += in - out;
+                const int yc = ybase + j - R;
+                const float2 cy = rowC[j];
+                const float n = cy.x * nxf, inv = cy.y * inv_nx;
+                if (n > 0.f) {
+                    const float c0 = v * inv;
+                    const float C = fmaf(fmaf(-c0, n, v), inv, c0);
+                    const float xv = (j >= R) ? cur[j - R][t + R] : prev[B + j - R][t + R];
+                    st1(Xr + (int64_t)yc * W + xs, xv - C);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// D at pixel (y, x) of distinct row `row`: the plain F-term sum over the raw
+// ring in subband order, as the shift-sum kernel forms it.
+template <typename TS>
+__device__ __forceinline__ float raw_sum(const TS* ring, const int16_t* lagrow, int F, int depth, int Tmod,
+                                         int64_t P, int64_t pix) {
+    float acc = 0.f;
+    for (int f = 0; f < F; ++f) {
+        int slot = Tmod - (int)__ldg(lagrow + f);
+        if (slot < 0) slot += depth;
+        float x = ld1(ring + ((int64_t)slot * F + f) * P + pix);
+        acc = (f == 0) ? x : acc + x;
+    }
+    return acc;
+}
+
+struct ResArgs {
+    FilterArgs a;            // R images in a.D, emission, stats
+    const void* raw;         // raw ring (storage type), for the 3x3 maximum of D
+    const int16_t* lag;      // [n_distinct][F]
+    int F, depth, Tmod;
+};
+
+// Candidates of one image row of a warp: 3x3 local maximum of D (clipped to the
+// image, ties count), then one warp-aggregated reservation and one record per
+// DM trial of the delay row.  Every lane of the warp calls it.
+template <typename TS>
+__device__ __noinline__ void emit_res_candidates(const ResArgs& ra, int row, int ys, int xs, float snr,
+                                                 bool cand, int m0, int nm) {
+    const FilterArgs& a = ra.a;
+    const int H = a.H, W = a.W;
+    const int lane = threadIdx.x & 31;
+    if (cand) {
+        const TS* ring = static_cast<const TS*>(ra.raw);
+        const int16_t* lr = ra.lag + (int64_t)row * ra.F;
+        const float dv = raw_sum(ring, lr, ra.F, ra.depth, ra.Tmod, a.P, (int64_t)ys * W + xs);
+        for (int dy = -1; dy <= 1 && cand; ++dy)
+            for (int dx = -1; dx <= 1 && cand; ++dx) {
+                if (dy == 0 && dx == 0) continue;
+                int yy = ys + dy, xx = xs + dx;
+                if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                if (raw_sum(ring, lr, ra.F, ra.depth, ra.Tmod, a.P, (int64_t)yy * W + xx) > dv) cand = false;
+            }
+    }
+    unsigned bal = __ballot_sync(0xffffffffu, cand);
+    if (!bal) return;
+    int leader = __ffs(bal) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(a.counter, (unsigned)(__popc(bal) * nm));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (cand) {
+        unsigned rank = __popc(bal & ((1u << lane) - 1u));
+        uint64_t pix = ((uint64_t)ys << a.bx) | (uint64_t)xs;
+        for (int m = 0; m < nm; ++m) {
+            unsigned idx = base + rank * nm + m;
+            if (idx < (unsigned)a.cap) {
+                a.keys[idx] = ((uint64_t)a.member_ord[m0 + m] << (a.bx + a.by)) | pix;
+                a.vals[idx] = snr;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_filter_res: per distinct row (blockIdx.y) and 128-column strip, streaming
+// down in blocks of B rows with a triple buffer of R rows (cp.async prefetch of
+// block k+1 while block k is processed; block k-1 still holds the lagged rows):
+//   2. horizontal window sums of R^2 (two stacks)                -> hE
+//   3. per column: vertical window sum as the suffix of the previous (2r+1)-row
+//      segment plus the prefix of the current one (exact) -> S(ys), ys = row - r;
+//      snr = R(ys)/sqrt(S), stats, threshold, candidates.
+template <int R, typename TS>
+__global__ void __launch_bounds__(ResGeom<R>::NT, 3) k_filter_res(ResArgs ra) {
+    using G = ResGeom<R>;
+    constexpr int TX = G::TX, B = G::B, L = G::L, SD = G::SD, SX = G::SX, WD = G::WD, NT = G::NT;
+    extern __shared__ float sm[];
+    float* Rb = sm;                     // [3][B][SD] R rows; col = x - (x0 - r)
+    float* hE = Rb + 3 * B * SD;        // [B][SX]
+    __shared__ float2 rowS[B];
+    const FilterArgs& a = ra.a;
+    const int strip = blockIdx.x, row = blockIdx.y;
+    const int x0 = strip * TX;
+    const int H = a.H, W = a.W;
+    const float* Rimg = a.D + (int64_t)row * a.P;
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int xs = x0 + t;
+    const bool col_s = t < TX && xs < W;
+    const int nx = col_s ? min(xs + R, W - 1) - max(xs - R, 0) + 1 : 0;
+    const float inv_nx = col_s ? 1.0f / (float)nx : 0.f;
+    float raw[L], suf[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) { raw[i] = 0.f; suf[i] = 0.f; }
+    float pre = 0.f;
+    double d1 = 0.0, d2 = 0.0, dc = 0.0;
+    const int m0 = a.member_start[row], nm = a.member_start[row + 1] - m0;
+
+    auto load = [&](int kk) {
+        if (t >= WD) return;
+        float* dst = Rb + (kk % 3) * B * SD + t;
+        const int x = x0 - R + t;
+        const bool colok = x >= 0 && x < W;
+        const int yb = kk * B;
+        const float* src = Rimg + (int64_t)yb * W + x;
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            bool in = colok && yb + j < H;
+            cp_async4(dst + j * SD, in ? src : Rimg, in);
+            src += W;
+        }
+    };
+    const int nblk = (H + R + B - 1) / B;
+    load(0);
+    cp_async_commit();
+    for (int k = 0; k < nblk; ++k) {
+        const int ybase = k * B;
+        const float* cur = Rb + (k % 3) * B * SD;
+        const float* prev = Rb + ((k + 2) % 3) * B * SD;
+        if (k + 1 < nblk) load(k + 1);
+        cp_async_commit();
+        if (t < B) rowS[t] = row_count<R>(ybase + t - R, H);
+        asm volatile("cp.async.wait_group 1;\n" ::);
+        __syncthreads();
+        // ---- horizontal window sums of R^2 over buffer cols c .. c + 2r (output col x0 + c)
+        for (int it = t; it < B * G::NR; it += NT) {
+            int j = it % B, run = it / B;
+            int c0 = run * G::RR;
+            int len = min(G::RR, TX - c0);
+            const float* in = cur + j * SD;
+            float* out = hE + j * SX;
+            two_stack_run<R, G::RR>(c0, len, [&](int c) { float r = in[c]; return r * r; },
+                                    [&](int c, float v) { out[c] = v; });
+        }
+        __syncthreads();
+        // ---- vertical segment sums -> S for row ys = ybase + j - r; detect
+        {
+            float s1 = 0.f, s2 = 0.f, cnt = 0.f;
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                const int o = j % L;
+                const float in = col_s ? hE[j * SX + t] : 0.f;
+                raw[o] = in;
+                pre = (o == 0) ? in : pre + in;
+                const float Ssum = (o + 1 < L) ? suf[o + 1] + pre : pre;
+                if (o == L - 1) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int i = L - 1; i >= 1; --i) { acc += raw[i]; suf[i] = acc; }
+                }
+                const int ys = ybase + j - R;
+                const float2 sy = rowS[j];
+                const float S = Ssum * (sy.y * inv_nx);
+                const bool valid = col_s && sy.x > 0.f && S > 0.f;
+                float snr = 0.f;
+                if (valid) {
+                    const float rv = (j >= R) ? cur[(j - R) * SD + t + R] : prev[(B + j - R) * SD + t + R];
+                    snr = rv * rsqrtf(S);
+                    s1 += snr;
+                    s2 = fmaf(snr, snr, s2);
+                    cnt += 1.f;
+                }
+                const bool cand = valid && snr > a.kappa;
+                if (__any_sync(0xffffffffu, cand))
+                    emit_res_candidates<TS>(ra, row, ys, xs, snr, cand, m0, nm);
+            }
+            d1 += s1;
+            d2 += s2;
+            dc += cnt;
+        }
+        __syncthreads();
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        d1 += __shfl_down_sync(0xffffffffu, d1, o);
+        d2 += __shfl_down_sync(0xffffffffu, d2, o);
+        dc += __shfl_down_sync(0xffffffffu, dc, o);
+    }
+    __shared__ double red[NT / 32][3];
+    if (lane == 0) { red[t >> 5][0] = d1; red[t >> 5][1] = d2; red[t >> 5][2] = dc; }
+    __syncthreads();
+    if (t == 0) {
+        double q1 = 0, q2 = 0, qc = 0;
+        for (int w = 0; w < NT / 32; ++w) { q1 += red[w][0]; q2 += red[w][1]; qc += red[w][2]; }
+        double* p = a.partials + ((int64_t)row * gridDim.x + strip) * 3;
+        p[0] = q1; p[1] = q2; p[2] = qc;
+    }
+}
+
+template <int R>
+constexpr size_t residual_smem_bytes() {
+    return ((size_t)2 * ResGeom<R>::B * ResGeom<R>::SD + (size_t)ResGeom<R>::B * ResGeom<R>::SX) * sizeof(float);
+}
+
+template <int R>
+constexpr size_t res_filter_smem_bytes() {
+    return ((size_t)3 * ResGeom<R>::B * ResGeom<R>::SD + (size_t)ResGeom<R>::B * ResGeom<R>::SX) * sizeof(float);
+}
+
+}  // namespace lpf

@@ -8,7 +8,7 @@
 // and records an event; poll waits on that event with a deadline.
 #include "../../include/lpf.h"
 #include "lpf_kernels.cuh"
-#include "lpf_filter_stream.cuh"
+#include "lpf_residual.cuh"
 
 #include <algorithm>
 #include <chrono>
@@ -107,7 +107,8 @@ struct lpf_stream {
     int tiles_x = 0, tiles_y = 0;
     size_t filter_smem = 0;
     int filter_rmax = 16;
-    bool stream_filter = false;     // streaming column-strip kernel (box_r 7 or 15)
+    bool stream_filter = false;     // residual path: k_residual + k_filter_res (box_r 7 or 15)
+    void* resring = nullptr;        // [depth][F][P] per-subband residual X - C(X), storage type
     int n_strips = 0;
 
     bool profiling = false;
@@ -145,7 +146,7 @@ void free_all(lpf_stream* s) {
     if (!s) return;
     cudaSetDevice(s->dev);
     if (s->st) cudaStreamSynchronize(s->st);
-    void* ptrs[] = {s->ring, s->D, s->stage, s->d_lag, s->d_chg, s->d_member_start, s->d_member_ord,
+    void* ptrs[] = {s->ring, s->resring, s->D, s->stage, s->d_lag, s->d_chg, s->d_member_start, s->d_member_ord,
                     s->d_ord2d, s->d_dmax, s->keys[0], s->keys[1], s->vals[0], s->vals[1],
                     s->d_counter, s->d_hist, s->d_partials, s->d_yx};
     for (void* p : ptrs)
@@ -249,9 +250,51 @@ void launch_ingest(lpf_stream* s, const float* frame, int64_t slot) {
 }
 
 template <typename TS>
+void launch_residual(lpf_stream* s, int64_t slot) {
+    const TS* raw = reinterpret_cast<const TS*>(s->ring) + slot * s->F * s->P;
+    TS* res = reinterpret_cast<TS*>(s->resring) + slot * s->F * s->P;
+    dim3 grid((unsigned)s->n_strips, (unsigned)s->F);
+    if (s->prm.box_r == 7)
+        lpf::k_residual<7, TS><<<grid, lpf::ResGeom<7>::NT, lpf::residual_smem_bytes<7>(), s->st>>>(raw, res, s->H, s->W, s->P);
+    else
+        lpf::k_residual<15, TS><<<grid, lpf::ResGeom<15>::NT, lpf::residual_smem_bytes<15>(), s->st>>>(raw, res, s->H, s->W, s->P);
+}
+
+template <typename TS>
+void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows, int Tmod) {
+    lpf::ResArgs ra;
+    ra.a = a;
+    ra.raw = s->ring;
+    ra.lag = s->d_lag;
+    ra.F = s->F;
+    ra.depth = s->depth;
+    ra.Tmod = Tmod;
+    dim3 grid((unsigned)s->n_strips, (unsigned)n_rows);
+    if (s->prm.box_r == 7)
+        lpf::k_filter_res<7, TS><<<grid, lpf::ResGeom<7>::NT, lpf::res_filter_smem_bytes<7>(), s->st>>>(ra);
+    else
+        lpf::k_filter_res<15, TS><<<grid, lpf::ResGeom<15>::NT, lpf::res_filter_smem_bytes<15>(), s->st>>>(ra);
+}
+
+template <typename TS>
+int set_res_attributes() {
+    if (cudaFuncSetAttribute(lpf::k_residual<7, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)lpf::residual_smem_bytes<7>()) != cudaSuccess ||
+        cudaFuncSetAttribute(lpf::k_residual<15, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)lpf::residual_smem_bytes<15>()) != cudaSuccess ||
+        cudaFuncSetAttribute(lpf::k_filter_res<7, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)lpf::res_filter_smem_bytes<7>()) != cudaSuccess ||
+        cudaFuncSetAttribute(lpf::k_filter_res<15, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)lpf::res_filter_smem_bytes<15>()) != cudaSuccess)
+        return LPF_E_CUDA;
+    return LPF_OK;
+}
+
+// Shift-sum over the residual ring (residual path: R = D - C) or the raw ring (D).
+template <typename TS>
 void launch_dedisperse(lpf_stream* s, int n_rows, int Tmod) {
     dim3 grid((unsigned)((s->P / 4 + 255) / 256));
-    const TS* ring = reinterpret_cast<const TS*>(s->ring);
+    const TS* ring = reinterpret_cast<const TS*>(s->stream_filter ? s->resring : s->ring);
     if (s->F <= 8)
         lpf::k_dedisperse<8, TS><<<grid, 256, 0, s->st>>>(ring, s->D, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, s->P);
     else if (s->F <= 16)
@@ -315,6 +358,13 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
         case LPF_FP16: launch_ingest<__half>(s, frame_dev, ring_slot); break;
         default: launch_ingest<__nv_bfloat16>(s, frame_dev, ring_slot); break;
     }
+    if (s->stream_filter) {
+        switch (s->prm.dtype) {
+            case LPF_FP32: launch_residual<float>(s, ring_slot); break;
+            case LPF_FP16: launch_residual<__half>(s, ring_slot); break;
+            default: launch_residual<__nv_bfloat16>(s, ring_slot); break;
+        }
+    }
     lpf::k_zero_u32<<<1, 32, 0, s->st>>>(s->d_counter, 1);
     prof_mark(s, sl, ST_DEDISP);
     if (n_rows > 0) {
@@ -333,11 +383,11 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
         a.keys = s->keys[0]; a.vals = s->vals[0]; a.counter = s->d_counter; a.cap = s->prm.cand_cap;
         a.bx = s->bx; a.by = s->by; a.partials = s->d_partials;
         if (s->stream_filter) {
-            dim3 grid((unsigned)s->n_strips, (unsigned)n_rows);
-            if (s->prm.box_r == 7)
-                lpf::k_filter_stream<7><<<grid, lpf::kStreamThreads, s->filter_smem, s->st>>>(a);
-            else
-                lpf::k_filter_stream<15><<<grid, lpf::kStreamThreads, s->filter_smem, s->st>>>(a);
+            switch (s->prm.dtype) {
+                case LPF_FP32: launch_filter_res<float>(s, a, n_rows, Tmod); break;
+                case LPF_FP16: launch_filter_res<__half>(s, a, n_rows, Tmod); break;
+                default: launch_filter_res<__nv_bfloat16>(s, a, n_rows, Tmod); break;
+            }
         } else {
             dim3 grid((unsigned)(s->tiles_x * s->tiles_y), (unsigned)n_rows);
             if (s->filter_rmax == 8)
@@ -481,8 +531,7 @@ int plan_stream(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, 
     s->filter_smem = filter_smem_bytes(prm.box_r, s->filter_rmax);
     s->stream_filter = prm.filter_impl == 2 || (prm.filter_impl == 0 && (prm.box_r == 7 || prm.box_r == 15));
     s->n_strips = (W + lpf::kStreamTX - 1) / lpf::kStreamTX;
-    if (s->stream_filter)
-        s->filter_smem = (prm.box_r == 7 ? lpf::StreamGeom<7>::smem_floats : lpf::StreamGeom<15>::smem_floats) * sizeof(float);
+
     *out = s;
     return LPF_OK;
 }
@@ -492,7 +541,7 @@ int plan_stream(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, 
 size_t footprint_bytes(const lpf_stream* s) {
     auto b = [](size_t n) { return std::max<size_t>(n, 16); };
     const size_t nd = (size_t)s->n_distinct, cap = (size_t)s->prm.cand_cap;
-    size_t t = (size_t)s->depth * s->F * s->P * s->elem;
+    size_t t = (size_t)s->depth * s->F * s->P * s->elem * (s->stream_filter ? 2 : 1);
     t += b(nd * s->P * 4) + b((size_t)s->F * s->HW * 4) + b(nd * s->F * 2) + b(nd * 4);
     t += b(s->member_start.size() * 4) + b(s->member_ord.size() * 4) + 2 * b((size_t)s->n_dm * 4);
     t += 2 * (b(cap * 8) + b(cap * 4)) + b(16) + b((size_t)256 * kSortBlocks * 4);
@@ -542,16 +591,20 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
                                             (int)filter_smem_bytes(8, 8)) != cudaSuccess) rc = LPF_E_CUDA;
     if (rc == LPF_OK && cudaFuncSetAttribute(lpf::k_filter<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)filter_smem_bytes(16, 16)) != cudaSuccess) rc = LPF_E_CUDA;
-    if (rc == LPF_OK && cudaFuncSetAttribute(lpf::k_filter_stream<7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)(lpf::StreamGeom<7>::smem_floats * sizeof(float))) != cudaSuccess) rc = LPF_E_CUDA;
-    if (rc == LPF_OK && cudaFuncSetAttribute(lpf::k_filter_stream<15>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)(lpf::StreamGeom<15>::smem_floats * sizeof(float))) != cudaSuccess) rc = LPF_E_CUDA;
+    if (rc == LPF_OK) rc = set_res_attributes<float>();
+    if (rc == LPF_OK) rc = set_res_attributes<__half>();
+    if (rc == LPF_OK) rc = set_res_attributes<__nv_bfloat16>();
     const size_t ring_elems = (size_t)buffer_depth * F * s->P;
     if (rc == LPF_OK) {
         if (cudaMalloc(&s->ring, ring_elems * s->elem) != cudaSuccess) { cudaGetLastError(); rc = LPF_E_OOM; }
         else s->device_bytes += ring_elems * s->elem;
     }
     if (rc == LPF_OK && cudaMemsetAsync(s->ring, 0, ring_elems * s->elem, s->st) != cudaSuccess) rc = LPF_E_CUDA;
+    if (rc == LPF_OK && s->stream_filter) {
+        if (cudaMalloc(&s->resring, ring_elems * s->elem) != cudaSuccess) { cudaGetLastError(); rc = LPF_E_OOM; }
+        else s->device_bytes += ring_elems * s->elem;
+        if (rc == LPF_OK && cudaMemsetAsync(s->resring, 0, ring_elems * s->elem, s->st) != cudaSuccess) rc = LPF_E_CUDA;
+    }
     if (rc == LPF_OK) rc = dev_alloc(s, &s->D, (size_t)s->n_distinct * s->P);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->stage, (size_t)F * s->HW);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_lag, (size_t)s->n_distinct * F);

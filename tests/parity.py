@@ -28,6 +28,17 @@ def cached_frames(stream, dtype: str = "fp32", maxsize: int = 256):
     return frame_at
 
 
+def cached_residuals(stream, dtype: str, r: int, maxsize: int = 256):
+    """Per-subband residuals X - C(X) of the storage-rounded frames, rounded to the
+    storage type: what a reduced-precision residual ring holds."""
+    raw = cached_frames(stream, dtype, maxsize)
+
+    @functools.lru_cache(maxsize=maxsize)
+    def res_at(t: int):
+        return O.storage_round(O.residual_frame(raw(t), r), dtype)
+    return res_at
+
+
 def neighbourhood_max(a: np.ndarray) -> np.ndarray:
     H, W = a.shape
     pad = np.full((H + 2, W + 2), -np.inf)
@@ -71,16 +82,22 @@ def compare_trial(gpu: np.ndarray, m: dict, F: int, kappa: float) -> Tuple[int, 
 
 
 def compare_push(gpu: np.ndarray, frame_at, T: int, delays: np.ndarray, r: int, kappa: float,
-                 dms=None, T_first: int = 0, gpu_stats: np.ndarray = None) -> Dict[str, float]:
-    """Compare all trials (or the listed ones) of one push with the oracle."""
+                 dms=None, T_first: int = 0, gpu_stats: np.ndarray = None,
+                 res_at=None) -> Dict[str, float]:
+    """Compare all trials (or the listed ones) of one push with the oracle
+    (with res_at: the residual-form reference of a reduced-precision ring)."""
     F = delays.shape[1]
     if dms is None:
         dms = O.active_trials(delays, T, T_first)
         # every GPU candidate must belong to an active trial
         assert set(np.unique(gpu["dm_idx"]).tolist()) <= set(dms)
     dmax = delays.max(axis=1)
-    _, stats, maps = O.search_push(frame_at, T, delays, r, kappa, T_first=T_first, dms=dms,
-                                   keep_maps=True)
+    if res_at is None:
+        _, stats, maps = O.search_push(frame_at, T, delays, r, kappa, T_first=T_first, dms=dms,
+                                       keep_maps=True)
+    else:
+        _, stats, maps = O.search_push_residual(frame_at, res_at, T, delays, r, kappa,
+                                                T_first=T_first, dms=dms, keep_maps=True)
     tot_n = tot_x = 0
     worst = 0.0
     for d in dms:

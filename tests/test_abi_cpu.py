@@ -80,11 +80,13 @@ def test_footprint_is_planned_without_a_gpu():
     fp32 = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth)
     fp16 = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth, dtype="fp16")
     ring32 = sp.depth * sp.F * sp.H * sp.W * 4
-    # ring + 205 dedispersed images + candidate buffers
-    assert ring32 + 205 * sp.H * sp.W * 4 < fp32 < ring32 + 205 * sp.H * sp.W * 4 + 400 * 2 ** 20
-    assert fp32 - fp16 == ring32 // 2
+    # raw ring + residual ring (box 31 uses the residual path) + 205 images + candidate buffers
+    assert 2 * ring32 + 205 * sp.H * sp.W * 4 < fp32 < 2 * ring32 + 205 * sp.H * sp.W * 4 + 400 * 2 ** 20
+    assert fp32 - fp16 == ring32
     deeper = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth + 10)
-    assert deeper - fp32 == 10 * sp.F * sp.H * sp.W * 4
+    assert deeper - fp32 == 2 * 10 * sp.F * sp.H * sp.W * 4
+    tiled = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth, filter_impl="tiled")
+    assert fp32 - tiled == ring32
     with pytest.raises(lpf.LpfError) as e:
         lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, 40)
     assert e.value.code == lpf.LPF_E_DEPTH
@@ -98,4 +100,4 @@ def test_stress_config_depth_96_is_rejected():
         lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth, dtype="fp16")
     assert e.value.code == lpf.LPF_E_DEPTH
     fp = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, 114, dtype="fp16")
-    assert 40e9 < fp < 50e9        # 30.6 GB ring + 13.5 GB dedispersed images
+    assert 70e9 < fp < 80e9        # 2 x 30.6 GB rings (raw, residual) + 13.8 GB images

@@ -4,7 +4,7 @@ import pytest
 
 import synth
 from oracle import lpf_oracle as O
-from tests.parity import assert_sorted_unique, cached_frames, compare_push
+from tests.parity import assert_sorted_unique, cached_frames, cached_residuals, compare_push
 
 pytestmark = pytest.mark.gpu
 
@@ -45,6 +45,7 @@ def test_aartfaac_bands_256px(lib, dtype):
     spec = synth.spec_aartfaac(H=256, W=256, n_sources=40, n_pulses=6, n_frames=80)
     st = synth.SyntheticStream(spec, seed=7)
     fa = cached_frames(st, dtype)
+    ra = None if dtype == "fp32" else cached_residuals(st, dtype, spec.box_r)
     delays = O.delay_table(spec.freqs_mhz, spec.dm_grid, spec.cadence_s)
     checks = {10, 47, 48, 61}
     with _open(lib, spec, dtype=dtype) as s:
@@ -55,7 +56,8 @@ def test_aartfaac_bands_256px(lib, dtype):
             assert Tp == T and not trunc
             if T in checks:
                 assert_sorted_unique(c)
-                res = compare_push(c, fa, T, delays, spec.box_r, spec.kappa, gpu_stats=s.stats())
+                res = compare_push(c, fa, T, delays, spec.box_r, spec.kappa, gpu_stats=s.stats(),
+                                   res_at=ra)
                 assert res["matched"] > 0
 
 

@@ -1,7 +1,8 @@
 """Reduced-precision ring storage: parity and the precision report.
 
-Parity: FP16/BF16 storage against the oracle run on the storage-rounded frames
-(the CUDA path computes in FP32 from the rounded values).  Report: S/N error
+Parity: FP16/BF16 storage against the oracle run on what the rings hold: the
+storage-rounded frames (for D) and the storage-rounded per-subband residuals
+X - C(X) (for D - C); the CUDA path computes in FP32 from those values.  Report: S/N error
 and candidate-set difference against the oracle on the unrounded FP32 frames,
 on the 2048^2 precision workload's bands and DM grid (501 trials, depth 48)
 at 512^2.  FP16 must stay within 2e-3 relative S/N error.
@@ -13,7 +14,7 @@ import pytest
 
 import synth
 from oracle import lpf_oracle as O
-from tests.parity import cached_frames, compare_push, ambiguous_mask
+from tests.parity import cached_frames, cached_residuals, compare_push, ambiguous_mask
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -55,7 +56,8 @@ def test_precision_report(lib, capsys):
                 _, c, n, _ = s.poll(timeout_ms=60000)
             # parity against the oracle on the values the ring holds
             compare_push(c, cached_frames(st, dtype), T, delays, spec.box_r, spec.kappa, dms=DMS,
-                         gpu_stats=s.stats())
+                         gpu_stats=s.stats(),
+                         res_at=None if dtype == "fp32" else cached_residuals(st, dtype, spec.box_r))
             worst, sym, matched = precision_vs_unrounded(c, unrounded, T, delays, spec.box_r,
                                                          spec.kappa, DMS)
             report[dtype] = dict(max_rel_snr_err=worst, sym_diff=sym, matched=matched, n_total=n)

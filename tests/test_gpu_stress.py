@@ -22,7 +22,10 @@ def test_stress_sampled_trials_and_dynspec(lib):
     st = synth.SyntheticStream(spec, seed=50)
     pool = [st.frame(t) for t in range(12)]
     pool[5][:, 1000, :] += 10.0                      # one broadband RFI stripe in the cycle
-    frame_at = lambda t: O.storage_round(pool[t % 12], "fp16")
+    raw_pool = [O.storage_round(p, "fp16") for p in pool]
+    res_pool = [O.storage_round(O.residual_frame(p, spec.box_r), "fp16") for p in raw_pool]
+    frame_at = lambda t: raw_pool[t % 12]
+    res_at = lambda t: res_pool[t % 12]
     delays = O.delay_table(spec.freqs_mhz, spec.dm_grid, spec.cadence_s)
     T = int(delays.max()) + 3
     dev_pool = [torch.from_numpy(p).cuda() for p in pool]
@@ -34,7 +37,7 @@ def test_stress_sampled_trials_and_dynspec(lib):
         assert not trunc
         assert_sorted_unique(c)
         compare_push(c, frame_at, T, delays, spec.box_r, spec.kappa, dms=[0, 1, 400, 1000],
-                     gpu_stats=s.stats())
+                     gpu_stats=s.stats(), res_at=res_at)
         Tw = 64
         ds = s.dynspec(c, Tw)                              # contiguous [n][32][64] FP32 batch
         assert ds.shape == (len(c), 32, Tw) and ds.is_contiguous()

@@ -386,3 +386,19 @@ def test_pins_catch_planted_shift_sign():
     _, D = wrong_dedisperse(_frames_from_array(arr), 7, delays, 0)
     _, Dok = O.dedisperse(_frames_from_array(arr), 7, delays, 0)
     assert Dok[0, 0] == 1.0 and D[0, 0] != 1.0
+
+
+def test_residual_form_equals_direct_form():
+    """Linearity of the local centre: sum_f (X_f - C(X_f)) shifted = D - C (Sec. 2.1.1)."""
+    spec = synth.spec_tiny(H=40, W=52, box_r=5, kappa=3.0, n_sources=6)
+    st = synth.SyntheticStream(spec, seed=31)
+    delays = O.delay_table(spec.freqs_mhz, spec.dm_grid, spec.cadence_s)
+    raw = lambda t: st.frame(t).astype(np.float64)
+    res = lambda t: O.residual_frame(raw(t), spec.box_r)
+    for T in (3, 9):
+        a, sa, ma = O.search_push(raw, T, delays, spec.box_r, spec.kappa, keep_maps=True)
+        b, sb, mb = O.search_push_residual(raw, res, T, delays, spec.box_r, spec.kappa, keep_maps=True)
+        assert [c[:4] for c in a] == [c[:4] for c in b] and len(a) > 0
+        for d in ma:
+            np.testing.assert_allclose(ma[d]["snr"], mb[d]["snr"], rtol=0, atol=1e-9)
+            assert abs(sa[d][1] - sb[d][1]) < 1e-12
