@@ -110,12 +110,14 @@ __global__ void __launch_bounds__(ResGeom<R>::NT) k_residual(const TS* __restric
 }
 
 // ---------------------------------------------------------------------------
-// D at pixel (y, x) of distinct row `row`: the plain F-term sum over the raw
-// ring in subband order, as the shift-sum kernel forms it.
+// D at pixel pix of a distinct delay row: the plain F-term sum over the raw
+// ring in subband order, as the shift-sum kernel forms it (loads unrolled so
+// they are in flight together).
 template <typename TS>
 __device__ __forceinline__ float raw_sum(const TS* ring, const int16_t* lagrow, int F, int depth, int Tmod,
                                          int64_t P, int64_t pix) {
     float acc = 0.f;
+#pragma unroll 8
     for (int f = 0; f < F; ++f) {
         int slot = Tmod - (int)__ldg(lagrow + f);
         if (slot < 0) slot += depth;
@@ -132,26 +134,32 @@ struct ResArgs {
     int F, depth, Tmod;
 };
 
-// Candidates of one image row of a warp: 3x3 local maximum of D (clipped to the
-// image, ties count), then one warp-aggregated reservation and one record per
-// DM trial of the delay row.  Every lane of the warp calls it.
+// Candidates of one image row of a warp (lanes with cand set): the 3x3 local
+// maximum of D clipped to the image (ties count), evaluated cooperatively: for
+// each candidate lane in turn, lanes 0..8 form D at the 9 pixels of its window
+// and a warp vote decides.  Then one warp-aggregated reservation and one
+// record per DM trial of the delay row.  Every lane of the warp calls it.
 template <typename TS>
 __device__ __noinline__ void emit_res_candidates(const ResArgs& ra, int row, int ys, int xs, float snr,
                                                  bool cand, int m0, int nm) {
     const FilterArgs& a = ra.a;
     const int H = a.H, W = a.W;
     const int lane = threadIdx.x & 31;
-    if (cand) {
-        const TS* ring = static_cast<const TS*>(ra.raw);
-        const int16_t* lr = ra.lag + (int64_t)row * ra.F;
-        const float dv = raw_sum(ring, lr, ra.F, ra.depth, ra.Tmod, a.P, (int64_t)ys * W + xs);
-        for (int dy = -1; dy <= 1 && cand; ++dy)
-            for (int dx = -1; dx <= 1 && cand; ++dx) {
-                if (dy == 0 && dx == 0) continue;
-                int yy = ys + dy, xx = xs + dx;
-                if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
-                if (raw_sum(ring, lr, ra.F, ra.depth, ra.Tmod, a.P, (int64_t)yy * W + xx) > dv) cand = false;
-            }
+    const TS* ring = static_cast<const TS*>(ra.raw);
+    const int16_t* lr = ra.lag + (int64_t)row * ra.F;
+    unsigned todo = __ballot_sync(0xffffffffu, cand);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int cy = __shfl_sync(0xffffffffu, ys, src), cx = __shfl_sync(0xffffffffu, xs, src);
+        const int yy = cy + lane / 3 - 1, xx = cx + lane % 3 - 1;
+        const bool in = lane < 9 && yy >= 0 && yy < H && xx >= 0 && xx < W;
+        float dv = 0.f;
+        if (in) dv = raw_sum(ring, lr, ra.F, ra.depth, ra.Tmod, a.P, (int64_t)yy * W + xx);
+        const float centre = __shfl_sync(0xffffffffu, dv, 4);
+        const bool higher = in && lane != 4 && dv > centre;
+        const bool is_max = !__any_sync(0xffffffffu, higher);
+        if (lane == src) cand = is_max;
     }
     unsigned bal = __ballot_sync(0xffffffffu, cand);
     if (!bal) return;
