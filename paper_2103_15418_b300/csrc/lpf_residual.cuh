@@ -7,9 +7,9 @@
 // with the same clipped window W(p) and count n_p for every plane.  So:
 //   k_residual   once per frame and subband: Xr = X - C(X) into a residual ring
 //   k_dedisperse over the residual ring gives R_d = D_d - C_d per distinct row
+//   k_dedisperse over the raw ring gives D_d, read only at candidate windows
 //   k_filter_res S_d = box mean of R_d^2, snr = R_d / sqrt(S_d), threshold,
-//                3x3 local maximum of D_d (formed from the raw ring at the
-//                candidate pixels only), stats, emission.
+//                3x3 local maximum of D_d, stats, emission.
 // One box filter per trial instead of two, with a halo of r instead of 2r.
 #pragma once
 #include "lpf_filter_stream.cuh"
@@ -110,56 +110,32 @@ __global__ void __launch_bounds__(ResGeom<R>::NT) k_residual(const TS* __restric
 }
 
 // ---------------------------------------------------------------------------
-// D at pixel pix of a distinct delay row: the plain F-term sum over the raw
-// ring in subband order, as the shift-sum kernel forms it (loads unrolled so
-// they are in flight together).
-template <typename TS>
-__device__ __forceinline__ float raw_sum(const TS* ring, const int16_t* lagrow, int F, int depth, int Tmod,
-                                         int64_t P, int64_t pix) {
-    float acc = 0.f;
-#pragma unroll 8
-    for (int f = 0; f < F; ++f) {
-        int slot = Tmod - (int)__ldg(lagrow + f);
-        if (slot < 0) slot += depth;
-        float x = ld1(ring + ((int64_t)slot * F + f) * P + pix);
-        acc = (f == 0) ? x : acc + x;
-    }
-    return acc;
-}
-
 struct ResArgs {
-    FilterArgs a;            // R images in a.D, emission, stats
-    const void* raw;         // raw ring (storage type), for the 3x3 maximum of D
-    const int16_t* lag;      // [n_distinct][F]
-    int F, depth, Tmod;
+    FilterArgs a;            // R = D - C images in a.D, emission, stats
+    const float* Dd;         // [n_rows][P] D images (shift-sum of the raw ring), for the 3x3 maximum
 };
 
 // Candidates of one image row of a warp (lanes with cand set): the 3x3 local
-// maximum of D clipped to the image (ties count), evaluated cooperatively: for
-// each candidate lane in turn, lanes 0..8 form D at the 9 pixels of its window
-// and a warp vote decides.  Then one warp-aggregated reservation and one
-// record per DM trial of the delay row.  Every lane of the warp calls it.
-template <typename TS>
+// maximum of D clipped to the image (ties count), from the dedispersed image of
+// the raw ring; then one warp-aggregated reservation and one record per DM
+// trial of the delay row.  Every lane of the warp calls it.
 __device__ __noinline__ void emit_res_candidates(const ResArgs& ra, int row, int ys, int xs, float snr,
                                                  bool cand, int m0, int nm) {
     const FilterArgs& a = ra.a;
     const int H = a.H, W = a.W;
     const int lane = threadIdx.x & 31;
-    const TS* ring = static_cast<const TS*>(ra.raw);
-    const int16_t* lr = ra.lag + (int64_t)row * ra.F;
-    unsigned todo = __ballot_sync(0xffffffffu, cand);
-    while (todo) {
-        const int src = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const int cy = __shfl_sync(0xffffffffu, ys, src), cx = __shfl_sync(0xffffffffu, xs, src);
-        const int yy = cy + lane / 3 - 1, xx = cx + lane % 3 - 1;
-        const bool in = lane < 9 && yy >= 0 && yy < H && xx >= 0 && xx < W;
-        float dv = 0.f;
-        if (in) dv = raw_sum(ring, lr, ra.F, ra.depth, ra.Tmod, a.P, (int64_t)yy * W + xx);
-        const float centre = __shfl_sync(0xffffffffu, dv, 4);
-        const bool higher = in && lane != 4 && dv > centre;
-        const bool is_max = !__any_sync(0xffffffffu, higher);
-        if (lane == src) cand = is_max;
+    if (cand) {
+        const float* p = ra.Dd + (int64_t)row * a.P + (int64_t)ys * W + xs;
+        float nb[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            int yy = ys + k / 3 - 1, xx = xs + k % 3 - 1;
+            nb[k] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? __ldg(p + (int64_t)(k / 3 - 1) * W + (k % 3 - 1))
+                                                             : -INFINITY;
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            if (k != 4 && nb[k] > nb[4]) cand = false;
     }
     unsigned bal = __ballot_sync(0xffffffffu, cand);
     if (!bal) return;
@@ -188,7 +164,7 @@ __device__ __noinline__ void emit_res_candidates(const ResArgs& ra, int row, int
 //   3. per column: vertical window sum as the suffix of the previous (2r+1)-row
 //      segment plus the prefix of the current one (exact) -> S(ys), ys = row - r;
 //      snr = R(ys)/sqrt(S), stats, threshold, candidates.
-template <int R, typename TS>
+template <int R>
 __global__ void __launch_bounds__(ResGeom<R>::NT, 3) k_filter_res(ResArgs ra) {
     using G = ResGeom<R>;
     constexpr int TX = G::TX, B = G::B, L = G::L, SD = G::SD, SX = G::SX, WD = G::WD, NT = G::NT;
@@ -280,7 +256,7 @@ __global__ void __launch_bounds__(ResGeom<R>::NT, 3) k_filter_res(ResArgs ra) {
                 }
                 const bool cand = valid && snr > a.kappa;
                 if (__any_sync(0xffffffffu, cand))
-                    emit_res_candidates<TS>(ra, row, ys, xs, snr, cand, m0, nm);
+                    emit_res_candidates(ra, row, ys, xs, snr, cand, m0, nm);
             }
             d1 += s1;
             d2 += s2;

@@ -109,6 +109,7 @@ struct lpf_stream {
     int filter_rmax = 16;
     bool stream_filter = false;     // residual path: k_residual + k_filter_res (box_r 7 or 15)
     void* resring = nullptr;        // [depth][F][P] per-subband residual X - C(X), storage type
+    float* Dd = nullptr;            // [n_distinct][P] D images of the residual path (local maxima)
     int n_strips = 0;
 
     bool profiling = false;
@@ -146,7 +147,7 @@ void free_all(lpf_stream* s) {
     if (!s) return;
     cudaSetDevice(s->dev);
     if (s->st) cudaStreamSynchronize(s->st);
-    void* ptrs[] = {s->ring, s->resring, s->D, s->stage, s->d_lag, s->d_chg, s->d_member_start, s->d_member_ord,
+    void* ptrs[] = {s->ring, s->resring, s->Dd, s->D, s->stage, s->d_lag, s->d_chg, s->d_member_start, s->d_member_ord,
                     s->d_ord2d, s->d_dmax, s->keys[0], s->keys[1], s->vals[0], s->vals[1],
                     s->d_counter, s->d_hist, s->d_partials, s->d_yx};
     for (void* p : ptrs)
@@ -260,20 +261,15 @@ void launch_residual(lpf_stream* s, int64_t slot) {
         lpf::k_residual<15, TS><<<grid, lpf::ResGeom<15>::NT, lpf::residual_smem_bytes<15>(), s->st>>>(raw, res, s->H, s->W, s->P);
 }
 
-template <typename TS>
-void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows, int Tmod) {
+void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows) {
     lpf::ResArgs ra;
     ra.a = a;
-    ra.raw = s->ring;
-    ra.lag = s->d_lag;
-    ra.F = s->F;
-    ra.depth = s->depth;
-    ra.Tmod = Tmod;
+    ra.Dd = s->Dd;
     dim3 grid((unsigned)s->n_strips, (unsigned)n_rows);
     if (s->prm.box_r == 7)
-        lpf::k_filter_res<7, TS><<<grid, lpf::ResGeom<7>::NT, lpf::res_filter_smem_bytes<7>(), s->st>>>(ra);
+        lpf::k_filter_res<7><<<grid, lpf::ResGeom<7>::NT, lpf::res_filter_smem_bytes<7>(), s->st>>>(ra);
     else
-        lpf::k_filter_res<15, TS><<<grid, lpf::ResGeom<15>::NT, lpf::res_filter_smem_bytes<15>(), s->st>>>(ra);
+        lpf::k_filter_res<15><<<grid, lpf::ResGeom<15>::NT, lpf::res_filter_smem_bytes<15>(), s->st>>>(ra);
 }
 
 template <typename TS>
@@ -282,25 +278,37 @@ int set_res_attributes() {
                              (int)lpf::residual_smem_bytes<7>()) != cudaSuccess ||
         cudaFuncSetAttribute(lpf::k_residual<15, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)lpf::residual_smem_bytes<15>()) != cudaSuccess ||
-        cudaFuncSetAttribute(lpf::k_filter_res<7, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(lpf::k_filter_res<7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)lpf::res_filter_smem_bytes<7>()) != cudaSuccess ||
-        cudaFuncSetAttribute(lpf::k_filter_res<15, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(lpf::k_filter_res<15>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)lpf::res_filter_smem_bytes<15>()) != cudaSuccess)
         return LPF_E_CUDA;
     return LPF_OK;
 }
 
-// Shift-sum over the residual ring (residual path: R = D - C) or the raw ring (D).
+// Shift-sum of a ring (raw: D; residual: R = D - C) into out.
+template <typename TS>
+void launch_dedisperse_ring(lpf_stream* s, const void* ring_v, float* out, int n_rows, int Tmod) {
+    dim3 grid((unsigned)((s->P / 4 + 255) / 256));
+    const TS* ring = reinterpret_cast<const TS*>(ring_v);
+    if (s->F <= 8)
+        lpf::k_dedisperse<8, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, s->P);
+    else if (s->F <= 16)
+        lpf::k_dedisperse<16, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, s->P);
+    else
+        lpf::k_dedisperse<32, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, s->P);
+}
+
+// Tiled path: D from the raw ring.  Residual path: D from the raw ring (for the
+// local maxima) and R = D - C from the residual ring.
 template <typename TS>
 void launch_dedisperse(lpf_stream* s, int n_rows, int Tmod) {
-    dim3 grid((unsigned)((s->P / 4 + 255) / 256));
-    const TS* ring = reinterpret_cast<const TS*>(s->stream_filter ? s->resring : s->ring);
-    if (s->F <= 8)
-        lpf::k_dedisperse<8, TS><<<grid, 256, 0, s->st>>>(ring, s->D, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, s->P);
-    else if (s->F <= 16)
-        lpf::k_dedisperse<16, TS><<<grid, 256, 0, s->st>>>(ring, s->D, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, s->P);
-    else
-        lpf::k_dedisperse<32, TS><<<grid, 256, 0, s->st>>>(ring, s->D, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, s->P);
+    if (s->stream_filter) {
+        launch_dedisperse_ring<TS>(s, s->ring, s->Dd, n_rows, Tmod);
+        launch_dedisperse_ring<TS>(s, s->resring, s->D, n_rows, Tmod);
+    } else {
+        launch_dedisperse_ring<TS>(s, s->ring, s->D, n_rows, Tmod);
+    }
 }
 
 template <typename TS>
@@ -383,11 +391,7 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
         a.keys = s->keys[0]; a.vals = s->vals[0]; a.counter = s->d_counter; a.cap = s->prm.cand_cap;
         a.bx = s->bx; a.by = s->by; a.partials = s->d_partials;
         if (s->stream_filter) {
-            switch (s->prm.dtype) {
-                case LPF_FP32: launch_filter_res<float>(s, a, n_rows, Tmod); break;
-                case LPF_FP16: launch_filter_res<__half>(s, a, n_rows, Tmod); break;
-                default: launch_filter_res<__nv_bfloat16>(s, a, n_rows, Tmod); break;
-            }
+            launch_filter_res(s, a, n_rows);
         } else {
             dim3 grid((unsigned)(s->tiles_x * s->tiles_y), (unsigned)n_rows);
             if (s->filter_rmax == 8)
@@ -542,7 +546,7 @@ size_t footprint_bytes(const lpf_stream* s) {
     auto b = [](size_t n) { return std::max<size_t>(n, 16); };
     const size_t nd = (size_t)s->n_distinct, cap = (size_t)s->prm.cand_cap;
     size_t t = (size_t)s->depth * s->F * s->P * s->elem * (s->stream_filter ? 2 : 1);
-    t += b(nd * s->P * 4) + b((size_t)s->F * s->HW * 4) + b(nd * s->F * 2) + b(nd * 4);
+    t += b(nd * s->P * 4) * (s->stream_filter ? 2 : 1) + b((size_t)s->F * s->HW * 4) + b(nd * s->F * 2) + b(nd * 4);
     t += b(s->member_start.size() * 4) + b(s->member_ord.size() * 4) + 2 * b((size_t)s->n_dm * 4);
     t += 2 * (b(cap * 8) + b(cap * 4)) + b(16) + b((size_t)256 * kSortBlocks * 4);
     t += b(nd * n_filter_blocks(s) * 3 * 8);
@@ -606,6 +610,7 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
         if (rc == LPF_OK && cudaMemsetAsync(s->resring, 0, ring_elems * s->elem, s->st) != cudaSuccess) rc = LPF_E_CUDA;
     }
     if (rc == LPF_OK) rc = dev_alloc(s, &s->D, (size_t)s->n_distinct * s->P);
+    if (rc == LPF_OK && s->stream_filter) rc = dev_alloc(s, &s->Dd, (size_t)s->n_distinct * s->P);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->stage, (size_t)F * s->HW);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_lag, (size_t)s->n_distinct * F);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_chg, (size_t)s->n_distinct);
