@@ -81,66 +81,39 @@ __global__ void k_ingest(const float* __restrict__ frame, TS* __restrict__ slot,
 }
 
 // ------------------------------------------------------------------ a3: shift-sum
-// plane[r][f] = ((Tmod - lag[r][f]) mod depth) * F + f: the ring plane that
-// subband f of distinct delay row r reads at this push (lag = frames back from
-// the newest frame, max_f delay - delay[r][f]).
-__global__ void k_plane_table(const int16_t* __restrict__ lag, int32_t* __restrict__ plane, int F,
-                              int depth, int Tmod, int n) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int slot = Tmod - (int)lag[i];
-    if (slot < 0) slot += depth;
-    plane[i] = slot * F + (i % F);
-}
-
-__device__ __forceinline__ void add2(float& ax, float& ay, float bx, float by) {
-    unsigned long long a, b, c;
-    asm("mov.b64 %0, {%1,%2};" : "=l"(a) : "f"(ax), "f"(ay));
-    asm("mov.b64 %0, {%1,%2};" : "=l"(b) : "f"(bx), "f"(by));
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(c) : "l"(a), "l"(b));
-    asm("mov.b64 {%0,%1}, %2;" : "=f"(ax), "=f"(ay) : "l"(c));
-}
-
-// D[r][p] = sum_{f=0..F-1} ring[plane[r][f]][p] for the distinct delay rows
-// r = 0 .. n_rows-1.  Each thread owns 4 consecutive pixels and walks every row
-// in order: the current plane value of each subband stays in registers and is
-// reloaded only when the row's plane of that subband differs from the previous
-// row's (bit f of chg[r]); the planes that change two rows ahead are prefetched
-// into L2.  The sum is formed afresh for every row in the order f = 0, ..., F-1
-// (FP32, two pixels per packed add), so its rounding is that of a plain F-term sum.
+// D[r][p] = sum_{f=0..F-1} ring[(Tmod - lag[r][f]) mod depth][f][p] for the
+// distinct delay rows r = 0 .. n_rows-1, lag[r][f] = max_f delay - delay[r][f]
+// (frames back from the newest frame).  Each thread owns 4 consecutive pixels
+// and walks every row in order: the current plane value of each subband stays
+// in registers and is reloaded only when the row's lag of that subband differs
+// from the previous row's (bit f of chg[r]).  The sum itself is formed afresh
+// for every row in the order f = 0, 1, ..., F-1 (FP32), so its rounding is
+// that of a plain F-term sum.
 template <int FMAX, typename TS>
 __global__ void __launch_bounds__(256) k_dedisperse(
-    const TS* __restrict__ ring, float* __restrict__ D, const int32_t* __restrict__ plane,
-    const uint32_t* __restrict__ chg, int F, int n_rows, int64_t P) {
-    constexpr int PF = 2;
+    const TS* __restrict__ ring, float* __restrict__ D, const int16_t* __restrict__ lag,
+    const uint32_t* __restrict__ chg, int F, int depth, int Tmod, int n_rows, int64_t P) {
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (q >= P) return;
     float4 cur[FMAX];
 #pragma unroll
     for (int f = 0; f < FMAX; ++f) cur[f] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int r = 0; r < n_rows; ++r) {
-        if (r + PF < n_rows) {
-            const uint32_t mp = __ldg(chg + r + PF);
-            const int32_t* pp = plane + (int64_t)(r + PF) * F;
-#pragma unroll
-            for (int f = 0; f < FMAX; ++f)
-                if (f < F && ((mp >> f) & 1u)) {
-                    const TS* addr = ring + (int64_t)__ldg(pp + f) * P + q;
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(addr));
-                }
-        }
         const uint32_t m = __ldg(chg + r);
-        const int32_t* pr = plane + (int64_t)r * F;
+        const int16_t* lr = lag + (int64_t)r * F;
 #pragma unroll
-        for (int f = 0; f < FMAX; ++f)
-            if (f < F && ((m >> f) & 1u)) cur[f] = ld4(ring + (int64_t)__ldg(pr + f) * P + q);
+        for (int f = 0; f < FMAX; ++f) {
+            if (f < F && ((m >> f) & 1u)) {
+                int slot = Tmod - (int)__ldg(lr + f);
+                if (slot < 0) slot += depth;
+                cur[f] = ld4(ring + ((int64_t)slot * F + f) * P + q);
+            }
+        }
         float4 acc = cur[0];
 #pragma unroll
-        for (int f = 1; f < FMAX; ++f)
-            if (f < F) {
-                add2(acc.x, acc.y, cur[f].x, cur[f].y);
-                add2(acc.z, acc.w, cur[f].z, cur[f].w);
-            }
+        for (int f = 1; f < FMAX; ++f) {
+            if (f < F) { acc.x += cur[f].x; acc.y += cur[f].y; acc.z += cur[f].z; acc.w += cur[f].w; }
+        }
         st4(D + (int64_t)r * P + q, acc);
     }
 }

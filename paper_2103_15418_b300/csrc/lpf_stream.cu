@@ -72,7 +72,6 @@ struct lpf_stream {
     float* stage = nullptr;          // host-push staging frame
     int16_t* d_lag = nullptr;
     uint32_t* d_chg = nullptr;      // per distinct row: subbands whose lag differs from the previous row
-    int32_t* d_plane = nullptr;     // [n_distinct][F] ring plane read by each row at the current push
     int* d_member_start = nullptr;
     int* d_member_ord = nullptr;
     int* d_ord2d = nullptr;
@@ -148,7 +147,7 @@ void free_all(lpf_stream* s) {
     if (!s) return;
     cudaSetDevice(s->dev);
     if (s->st) cudaStreamSynchronize(s->st);
-    void* ptrs[] = {s->ring, s->resring, s->Dd, s->D, s->stage, s->d_lag, s->d_chg, s->d_plane, s->d_member_start, s->d_member_ord,
+    void* ptrs[] = {s->ring, s->resring, s->Dd, s->D, s->stage, s->d_lag, s->d_chg, s->d_member_start, s->d_member_ord,
                     s->d_ord2d, s->d_dmax, s->keys[0], s->keys[1], s->vals[0], s->vals[1],
                     s->d_counter, s->d_hist, s->d_partials, s->d_yx};
     for (void* p : ptrs)
@@ -293,19 +292,17 @@ void launch_dedisperse_ring(lpf_stream* s, const void* ring_v, float* out, int n
     dim3 grid((unsigned)((s->P / 4 + 255) / 256));
     const TS* ring = reinterpret_cast<const TS*>(ring_v);
     if (s->F <= 8)
-        lpf::k_dedisperse<8, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_plane, s->d_chg, s->F, n_rows, s->P);
+        lpf::k_dedisperse<8, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, s->P);
     else if (s->F <= 16)
-        lpf::k_dedisperse<16, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_plane, s->d_chg, s->F, n_rows, s->P);
+        lpf::k_dedisperse<16, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, s->P);
     else
-        lpf::k_dedisperse<32, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_plane, s->d_chg, s->F, n_rows, s->P);
+        lpf::k_dedisperse<32, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, s->P);
 }
 
 // Tiled path: D from the raw ring.  Residual path: D from the raw ring (for the
 // local maxima) and R = D - C from the residual ring.
 template <typename TS>
 void launch_dedisperse(lpf_stream* s, int n_rows, int Tmod) {
-    const int n = n_rows * s->F;
-    lpf::k_plane_table<<<(n + 255) / 256, 256, 0, s->st>>>(s->d_lag, s->d_plane, s->F, s->depth, Tmod, n);
     if (s->stream_filter) {
         launch_dedisperse_ring<TS>(s, s->ring, s->Dd, n_rows, Tmod);
         launch_dedisperse_ring<TS>(s, s->resring, s->D, n_rows, Tmod);
@@ -550,7 +547,6 @@ size_t footprint_bytes(const lpf_stream* s) {
     const size_t nd = (size_t)s->n_distinct, cap = (size_t)s->prm.cand_cap;
     size_t t = (size_t)s->depth * s->F * s->P * s->elem * (s->stream_filter ? 2 : 1);
     t += b(nd * s->P * 4) * (s->stream_filter ? 2 : 1) + b((size_t)s->F * s->HW * 4) + b(nd * s->F * 2) + b(nd * 4);
-    t += b(nd * s->F * 4);
     t += b(s->member_start.size() * 4) + b(s->member_ord.size() * 4) + 2 * b((size_t)s->n_dm * 4);
     t += 2 * (b(cap * 8) + b(cap * 4)) + b(16) + b((size_t)256 * kSortBlocks * 4);
     t += b(nd * n_filter_blocks(s) * 3 * 8);
@@ -618,7 +614,6 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
     if (rc == LPF_OK) rc = dev_alloc(s, &s->stage, (size_t)F * s->HW);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_lag, (size_t)s->n_distinct * F);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_chg, (size_t)s->n_distinct);
-    if (rc == LPF_OK) rc = dev_alloc(s, &s->d_plane, (size_t)s->n_distinct * F);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_member_start, s->member_start.size());
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_member_ord, s->member_ord.size());
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_ord2d, (size_t)n_dm);
