@@ -286,17 +286,31 @@ int set_res_attributes() {
     return LPF_OK;
 }
 
-// Shift-sum of a ring (raw: D; residual: R = D - C) into out.
+// Shift-sum of a ring (raw: D; residual: R = D - C) into out; the rows are
+// split into two segments (each restarts its register state) for parallelism.
 template <typename TS>
 void launch_dedisperse_ring(lpf_stream* s, const void* ring_v, float* out, int n_rows, int Tmod) {
-    dim3 grid((unsigned)((s->P / 4 + 255) / 256));
-    const TS* ring = reinterpret_cast<const TS*>(ring_v);
-    if (s->F <= 8)
-        lpf::k_dedisperse<8, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, s->P);
-    else if (s->F <= 16)
-        lpf::k_dedisperse<16, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, s->P);
-    else
-        lpf::k_dedisperse<32, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, s->P);
+    const int nseg = n_rows >= 32 ? 2 : 1;
+    const int seg = (n_rows + nseg - 1) / nseg;
+    if constexpr (sizeof(TS) == 4) {
+        const float* ring = reinterpret_cast<const float*>(ring_v);
+        dim3 grid((unsigned)((s->P / 4 + 255) / 256), (unsigned)nseg);
+        if (s->F <= 8)
+            lpf::k_dedisperse<8><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, seg, s->P);
+        else if (s->F <= 16)
+            lpf::k_dedisperse<16><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, seg, s->P);
+        else
+            lpf::k_dedisperse<32><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, seg, s->P);
+    } else {
+        const TS* ring = reinterpret_cast<const TS*>(ring_v);
+        dim3 grid((unsigned)((s->P / 8 + 255) / 256), (unsigned)nseg);
+        if (s->F <= 8)
+            lpf::k_dedisperse16<8, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, seg, s->P);
+        else if (s->F <= 16)
+            lpf::k_dedisperse16<16, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, seg, s->P);
+        else
+            lpf::k_dedisperse16<32, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, seg, s->P);
+    }
 }
 
 // Tiled path: D from the raw ring.  Residual path: D from the raw ring (for the
