@@ -82,7 +82,7 @@ __global__ void k_ingest(const float* __restrict__ frame, TS* __restrict__ slot,
 
 // ------------------------------------------------------------------ a3: shift-sum
 // D[r][p] = sum_{f=0..F-1} ring[(Tmod - lag[r][f]) mod depth][f][p] for the
-// distinct delay rows r of [row_base, row_base + n_rows), lag[r][f] = max_f delay - delay[r][f] (frames back
+// distinct delay rows r, lag[r][f] = max_f delay - delay[r][f] (frames back
 // from the newest frame).  Each thread owns consecutive pixels (4 for FP32
 // storage, 8 for 16-bit storage, so every load is 16 bytes) and walks the rows
 // of one segment (blockIdx.y) in order: the current plane value of each subband
@@ -93,11 +93,10 @@ __global__ void k_ingest(const float* __restrict__ frame, TS* __restrict__ slot,
 template <int FMAX>
 __global__ void __launch_bounds__(256) k_dedisperse(
     const float* __restrict__ ring, float* __restrict__ D, const int16_t* __restrict__ lag,
-    const uint32_t* __restrict__ chg, int F, int depth, int Tmod, int row_base, int n_rows, int seg_rows,
-    int64_t P) {
+    const uint32_t* __restrict__ chg, int F, int depth, int Tmod, int n_rows, int seg_rows, int64_t P) {
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (q >= P) return;
-    const int r0 = row_base + blockIdx.y * seg_rows, r1 = min(row_base + n_rows, r0 + seg_rows);
+    const int r0 = blockIdx.y * seg_rows, r1 = min(n_rows, r0 + seg_rows);
     float4 cur[FMAX];
 #pragma unroll
     for (int f = 0; f < FMAX; ++f) cur[f] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -133,11 +132,10 @@ __device__ __forceinline__ float2 to_float2(unsigned u, const __nv_bfloat16*) {
 template <int FMAX, typename TS>
 __global__ void __launch_bounds__(256) k_dedisperse16(
     const TS* __restrict__ ring, float* __restrict__ D, const int16_t* __restrict__ lag,
-    const uint32_t* __restrict__ chg, int F, int depth, int Tmod, int row_base, int n_rows, int seg_rows,
-    int64_t P) {
+    const uint32_t* __restrict__ chg, int F, int depth, int Tmod, int n_rows, int seg_rows, int64_t P) {
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8;
     if (q >= P) return;
-    const int r0 = row_base + blockIdx.y * seg_rows, r1 = min(row_base + n_rows, r0 + seg_rows);
+    const int r0 = blockIdx.y * seg_rows, r1 = min(n_rows, r0 + seg_rows);
     uint4 cur[FMAX];
 #pragma unroll
     for (int f = 0; f < FMAX; ++f) cur[f] = make_uint4(0u, 0u, 0u, 0u);
@@ -224,7 +222,6 @@ struct FilterArgs {
     int cap;
     int bx, by;            // bits of x and y in the key
     double* partials;      // [n_rows][tiles][3]
-    int row_base;          // first distinct row of this launch (blockIdx.y + row_base)
 };
 
 __device__ __forceinline__ int odd_stride(int n) { return n | 1; }
@@ -247,7 +244,7 @@ __global__ void __launch_bounds__(kFilterThreads, 1) k_filter(FilterArgs a) {
     float* bufB = bufE + nC * sC;        // [nC][sB]  horizontal sums of E
 
     const int tile = blockIdx.x;
-    const int row = a.row_base + blockIdx.y;
+    const int row = blockIdx.y;
     const int ty = tile / a.tiles_x, tx = tile - ty * a.tiles_x;
     const int y0 = ty * kTile, x0 = tx * kTile;
     const int H = a.H, W = a.W;

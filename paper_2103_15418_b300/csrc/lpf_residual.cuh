@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(ResGeom<R>::NT, 3) k_filter_res(ResArgs ra) {
     float* hE = Rb + 3 * B * SD;        // [B][SX]
     __shared__ float2 rowS[B];
     const FilterArgs& a = ra.a;
-    const int strip = blockIdx.x, row = a.row_base + blockIdx.y;
+    const int strip = blockIdx.x, row = blockIdx.y;
     const int x0 = strip * TX;
     const int H = a.H, W = a.W;
     const float* Rimg = a.D + (int64_t)row * a.P;

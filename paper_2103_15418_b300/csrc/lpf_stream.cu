@@ -27,8 +27,6 @@ namespace {
 constexpr double kCdmSeconds = 4.148808e3;   // s MHz^2 cm^3 / pc (Sec. 3.2)
 constexpr int kSortBlocks = 148;
 constexpr int kMaxSlots = 16;
-constexpr int kGroups = 4;          // DM-row groups pipelined between the two lanes
-constexpr int kProfPairs = 24;
 
 enum Stage { ST_INGEST, ST_DEDISP, ST_FILTER, ST_SORT, ST_FORMAT, ST_STATS, ST_N };
 const char* kStageNames[ST_N] = {"ingest", "dedisperse", "filter_detect", "sort", "format", "stats"};
@@ -94,9 +92,6 @@ struct lpf_stream {
     cudaStream_t st = nullptr;
     bool own_stream = false;
     cudaStream_t copy_st = nullptr;
-    cudaStream_t st_b = nullptr;     // filter/ordering lane; s->st runs ingest and shift-sums
-    cudaEvent_t ev_dd[kGroups] = {}; // shift-sum of group g done (on st)
-    cudaEvent_t ev_b_done = nullptr; // everything of the push done (on st_b)
     Slot slots[kMaxSlots];
     int n_slots = 2;
     std::deque<int> pending;         // slot indices in push order
@@ -118,9 +113,7 @@ struct lpf_stream {
     int n_strips = 0;
 
     bool profiling = false;
-    cudaEvent_t ev[kMaxSlots][2 * kProfPairs] = {};
-    int prof_stage[kMaxSlots][kProfPairs] = {};
-    int prof_used[kMaxSlots] = {};
+    cudaEvent_t ev[kMaxSlots][ST_N + 1] = {};
     bool prof_slot[kMaxSlots] = {};
     double prof_ms[ST_N] = {};
     int64_t prof_n[ST_N] = {};
@@ -167,11 +160,6 @@ void free_all(lpf_stream* s) {
     for (auto& row : s->ev)
         for (auto& e : row)
             if (e) cudaEventDestroy(e);
-    for (auto& e : s->ev_dd)
-        if (e) cudaEventDestroy(e);
-    if (s->ev_b_done) cudaEventDestroy(s->ev_b_done);
-    if (s->st_b) cudaStreamSynchronize(s->st_b);
-    if (s->st_b) cudaStreamDestroy(s->st_b);
     if (s->h_count) cudaFreeHost(s->h_count);
     if (s->h_stats) cudaFreeHost(s->h_stats);
     if (s->copy_st) cudaStreamDestroy(s->copy_st);
@@ -279,9 +267,9 @@ void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows) {
     ra.Dd = s->Dd;
     dim3 grid((unsigned)s->n_strips, (unsigned)n_rows);
     if (s->prm.box_r == 7)
-        lpf::k_filter_res<7><<<grid, lpf::ResGeom<7>::NT, lpf::res_filter_smem_bytes<7>(), s->st_b>>>(ra);
+        lpf::k_filter_res<7><<<grid, lpf::ResGeom<7>::NT, lpf::res_filter_smem_bytes<7>(), s->st>>>(ra);
     else
-        lpf::k_filter_res<15><<<grid, lpf::ResGeom<15>::NT, lpf::res_filter_smem_bytes<15>(), s->st_b>>>(ra);
+        lpf::k_filter_res<15><<<grid, lpf::ResGeom<15>::NT, lpf::res_filter_smem_bytes<15>(), s->st>>>(ra);
 }
 
 template <typename TS>
@@ -301,39 +289,39 @@ int set_res_attributes() {
 // Shift-sum of a ring (raw: D; residual: R = D - C) into out; the rows are
 // split into two segments (each restarts its register state) for parallelism.
 template <typename TS>
-void launch_dedisperse_ring(lpf_stream* s, const void* ring_v, float* out, int row_base, int n_rows, int Tmod) {
+void launch_dedisperse_ring(lpf_stream* s, const void* ring_v, float* out, int n_rows, int Tmod) {
     const int nseg = n_rows >= 32 ? 2 : 1;
     const int seg = (n_rows + nseg - 1) / nseg;
     if constexpr (sizeof(TS) == 4) {
         const float* ring = reinterpret_cast<const float*>(ring_v);
         dim3 grid((unsigned)((s->P / 4 + 255) / 256), (unsigned)nseg);
         if (s->F <= 8)
-            lpf::k_dedisperse<8><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, row_base, n_rows, seg, s->P);
+            lpf::k_dedisperse<8><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, seg, s->P);
         else if (s->F <= 16)
-            lpf::k_dedisperse<16><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, row_base, n_rows, seg, s->P);
+            lpf::k_dedisperse<16><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, seg, s->P);
         else
-            lpf::k_dedisperse<32><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, row_base, n_rows, seg, s->P);
+            lpf::k_dedisperse<32><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, seg, s->P);
     } else {
         const TS* ring = reinterpret_cast<const TS*>(ring_v);
         dim3 grid((unsigned)((s->P / 8 + 255) / 256), (unsigned)nseg);
         if (s->F <= 8)
-            lpf::k_dedisperse16<8, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, row_base, n_rows, seg, s->P);
+            lpf::k_dedisperse16<8, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, seg, s->P);
         else if (s->F <= 16)
-            lpf::k_dedisperse16<16, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, row_base, n_rows, seg, s->P);
+            lpf::k_dedisperse16<16, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, seg, s->P);
         else
-            lpf::k_dedisperse16<32, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, row_base, n_rows, seg, s->P);
+            lpf::k_dedisperse16<32, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, seg, s->P);
     }
 }
 
 // Tiled path: D from the raw ring.  Residual path: D from the raw ring (for the
 // local maxima) and R = D - C from the residual ring.
 template <typename TS>
-void launch_dedisperse(lpf_stream* s, int row_base, int n_rows, int Tmod) {
+void launch_dedisperse(lpf_stream* s, int n_rows, int Tmod) {
     if (s->stream_filter) {
-        launch_dedisperse_ring<TS>(s, s->ring, s->Dd, row_base, n_rows, Tmod);
-        launch_dedisperse_ring<TS>(s, s->resring, s->D, row_base, n_rows, Tmod);
+        launch_dedisperse_ring<TS>(s, s->ring, s->Dd, n_rows, Tmod);
+        launch_dedisperse_ring<TS>(s, s->resring, s->D, n_rows, Tmod);
     } else {
-        launch_dedisperse_ring<TS>(s, s->ring, s->D, row_base, n_rows, Tmod);
+        launch_dedisperse_ring<TS>(s, s->ring, s->D, n_rows, Tmod);
     }
 }
 
@@ -359,37 +347,23 @@ size_t filter_smem_bytes(int r, int rmax) {
     return floats * sizeof(float);
 }
 
-// Profiling: an event pair around each launch group, on the stream it runs on.
-int prof_begin(lpf_stream* s, int sl, int stage, cudaStream_t st) {
-    if (!s->profiling || s->prof_used[sl] >= kProfPairs) return -1;
-    int k = s->prof_used[sl]++;
-    s->prof_stage[sl][k] = stage;
-    cudaEventRecord(s->ev[sl][2 * k], st);
-    return k;
-}
-
-void prof_end(lpf_stream* s, int sl, int k, cudaStream_t st) {
-    if (k >= 0) cudaEventRecord(s->ev[sl][2 * k + 1], st);
+void prof_mark(lpf_stream* s, int sl, int i) {
+    if (s->profiling) cudaEventRecord(s->ev[sl][i], s->st);
 }
 
 // Accumulate the stage times of a finished slot (its done event has completed).
 void prof_collect(lpf_stream* s, int sl) {
     if (!s->prof_slot[sl]) return;
-    bool seen[ST_N] = {};
-    for (int k = 0; k < s->prof_used[sl]; ++k) {
+    for (int i = 0; i < ST_N; ++i) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, s->ev[sl][2 * k], s->ev[sl][2 * k + 1]) == cudaSuccess) {
-            int st = s->prof_stage[sl][k];
-            s->prof_ms[st] += ms;
-            seen[st] = true;
+        if (cudaEventElapsedTime(&ms, s->ev[sl][i], s->ev[sl][i + 1]) == cudaSuccess) {
+            s->prof_ms[i] += ms;
+            s->prof_n[i] += 1;
         } else {
             cudaGetLastError();
         }
     }
-    for (int i = 0; i < ST_N; ++i)
-        if (seen[i]) s->prof_n[i] += 1;
     s->prof_slot[sl] = false;
-    s->prof_used[sl] = 0;
 }
 
 int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
@@ -400,9 +374,7 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
     const int n_rows = n_active_rows(s, T);
     cudaGetLastError();
 
-    s->prof_used[sl] = 0;
-    // lane A (s->st): ingest, then the shift-sums of the row groups
-    int pk = prof_begin(s, sl, ST_INGEST, s->st);
+    prof_mark(s, sl, ST_INGEST);
     switch (s->prm.dtype) {
         case LPF_FP32: launch_ingest<float>(s, frame_dev, ring_slot); break;
         case LPF_FP16: launch_ingest<__half>(s, frame_dev, ring_slot); break;
@@ -415,74 +387,57 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
             default: launch_residual<__nv_bfloat16>(s, ring_slot); break;
         }
     }
-    prof_end(s, sl, pk, s->st);
-    const int ngroups = n_rows >= 64 ? kGroups : 1;
-    const int gsize = (n_rows + ngroups - 1) / ngroups;
-    for (int g = 0; g < ngroups && n_rows > 0; ++g) {
-        const int rb = g * gsize, nr = std::min(gsize, n_rows - rb);
-        if (nr <= 0) break;
-        pk = prof_begin(s, sl, ST_DEDISP, s->st);
+    lpf::k_zero_u32<<<1, 32, 0, s->st>>>(s->d_counter, 1);
+    prof_mark(s, sl, ST_DEDISP);
+    if (n_rows > 0) {
         switch (s->prm.dtype) {
-            case LPF_FP32: launch_dedisperse<float>(s, rb, nr, Tmod); break;
-            case LPF_FP16: launch_dedisperse<__half>(s, rb, nr, Tmod); break;
-            default: launch_dedisperse<__nv_bfloat16>(s, rb, nr, Tmod); break;
+            case LPF_FP32: launch_dedisperse<float>(s, n_rows, Tmod); break;
+            case LPF_FP16: launch_dedisperse<__half>(s, n_rows, Tmod); break;
+            default: launch_dedisperse<__nv_bfloat16>(s, n_rows, Tmod); break;
         }
-        prof_end(s, sl, pk, s->st);
-        LPF_TRY(cudaEventRecord(s->ev_dd[g], s->st));
     }
-    // lane B (s->st_b): filter of each group once its shift-sum is done, then ordering and stats
-    lpf::k_zero_u32<<<1, 32, 0, s->st_b>>>(s->d_counter, 1);
-    for (int g = 0; g < ngroups && n_rows > 0; ++g) {
-        const int rb = g * gsize, nr = std::min(gsize, n_rows - rb);
-        if (nr <= 0) break;
-        LPF_TRY(cudaStreamWaitEvent(s->st_b, s->ev_dd[g], 0));
+    prof_mark(s, sl, ST_FILTER);
+    if (n_rows > 0) {
         lpf::FilterArgs a;
         a.D = s->D; a.P = s->P; a.H = s->H; a.W = s->W; a.r = s->prm.box_r; a.kappa = s->prm.kappa;
         a.tiles_x = s->tiles_x; a.tiles_y = s->tiles_y;
         a.member_start = s->d_member_start; a.member_ord = s->d_member_ord;
         a.keys = s->keys[0]; a.vals = s->vals[0]; a.counter = s->d_counter; a.cap = s->prm.cand_cap;
-        a.bx = s->bx; a.by = s->by; a.partials = s->d_partials; a.row_base = rb;
-        pk = prof_begin(s, sl, ST_FILTER, s->st_b);
+        a.bx = s->bx; a.by = s->by; a.partials = s->d_partials;
         if (s->stream_filter) {
-            launch_filter_res(s, a, nr);
+            launch_filter_res(s, a, n_rows);
         } else {
-            dim3 grid((unsigned)(s->tiles_x * s->tiles_y), (unsigned)nr);
+            dim3 grid((unsigned)(s->tiles_x * s->tiles_y), (unsigned)n_rows);
             if (s->filter_rmax == 8)
-                lpf::k_filter<8><<<grid, lpf::kFilterThreads, s->filter_smem, s->st_b>>>(a);
+                lpf::k_filter<8><<<grid, lpf::kFilterThreads, s->filter_smem, s->st>>>(a);
             else
-                lpf::k_filter<16><<<grid, lpf::kFilterThreads, s->filter_smem, s->st_b>>>(a);
+                lpf::k_filter<16><<<grid, lpf::kFilterThreads, s->filter_smem, s->st>>>(a);
         }
-        prof_end(s, sl, pk, s->st_b);
     }
-    pk = prof_begin(s, sl, ST_SORT, s->st_b);
+    prof_mark(s, sl, ST_SORT);
     int cur = 0;
     for (int shift = 0; shift < s->key_bits; shift += 8) {
-        lpf::k_rs_hist<<<kSortBlocks, lpf::kSortThreads, 0, s->st_b>>>(s->keys[cur], s->d_counter,
-                                                                         s->prm.cand_cap, shift, s->d_hist);
-        lpf::k_rs_scan<<<1, 1024, 0, s->st_b>>>(s->d_hist, kSortBlocks);
-        lpf::k_rs_scatter<<<kSortBlocks, lpf::kSortThreads, 0, s->st_b>>>(
+        lpf::k_rs_hist<<<kSortBlocks, lpf::kSortThreads, 0, s->st>>>(s->keys[cur], s->d_counter,
+                                                                       s->prm.cand_cap, shift, s->d_hist);
+        lpf::k_rs_scan<<<1, 1024, 0, s->st>>>(s->d_hist, kSortBlocks);
+        lpf::k_rs_scatter<<<kSortBlocks, lpf::kSortThreads, 0, s->st>>>(
             s->keys[cur], s->vals[cur], s->keys[cur ^ 1], s->vals[cur ^ 1], s->d_counter,
             s->prm.cand_cap, shift, s->d_hist);
         cur ^= 1;
     }
-    prof_end(s, sl, pk, s->st_b);
-    pk = prof_begin(s, sl, ST_FORMAT, s->st_b);
-    lpf::k_format<<<148 * 4, 256, 0, s->st_b>>>(s->keys[cur], s->vals[cur], s->d_counter, s->prm.cand_cap,
-                                                slot.d_out, s->d_ord2d, s->d_dmax, T, s->bx, s->by);
-    prof_end(s, sl, pk, s->st_b);
-    pk = prof_begin(s, sl, ST_STATS, s->st_b);
+    prof_mark(s, sl, ST_FORMAT);
+    lpf::k_format<<<148 * 4, 256, 0, s->st>>>(s->keys[cur], s->vals[cur], s->d_counter, s->prm.cand_cap,
+                                              slot.d_out, s->d_ord2d, s->d_dmax, T, s->bx, s->by);
+    prof_mark(s, sl, ST_STATS);
     if (n_rows > 0)
-        lpf::k_stats<<<n_rows, 256, 0, s->st_b>>>(s->d_partials, n_filter_blocks(s), slot.d_stats);
-    prof_end(s, sl, pk, s->st_b);
+        lpf::k_stats<<<n_rows, 256, 0, s->st>>>(s->d_partials, n_filter_blocks(s), slot.d_stats);
+    prof_mark(s, sl, ST_N);
     if (cudaGetLastError() != cudaSuccess) return LPF_E_CUDA;
-    LPF_TRY(cudaMemcpyAsync(s->h_count + sl, s->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st_b));
+    LPF_TRY(cudaMemcpyAsync(s->h_count + sl, s->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st));
     if (n_rows > 0)
         LPF_TRY(cudaMemcpyAsync(s->h_stats + (size_t)sl * s->n_distinct * 3, slot.d_stats,
-                                (size_t)n_rows * 3 * sizeof(double), cudaMemcpyDeviceToHost, s->st_b));
-    LPF_TRY(cudaEventRecord(slot.done, s->st_b));
-    // lane A joins lane B: the next push (and any caller work on s->st) follows this one
-    LPF_TRY(cudaEventRecord(s->ev_b_done, s->st_b));
-    LPF_TRY(cudaStreamWaitEvent(s->st, s->ev_b_done, 0));
+                                (size_t)n_rows * 3 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    LPF_TRY(cudaEventRecord(slot.done, s->st));
     s->prof_slot[sl] = s->profiling;
     slot.T = T;
     slot.n_active = n_rows;
@@ -650,10 +605,6 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
         s->own_stream = true;
     }
     if (cudaStreamCreateWithFlags(&s->copy_st, cudaStreamNonBlocking) != cudaSuccess) rc = LPF_E_CUDA;
-    if (rc == LPF_OK && cudaStreamCreateWithFlags(&s->st_b, cudaStreamNonBlocking) != cudaSuccess) rc = LPF_E_CUDA;
-    for (int g = 0; g < kGroups && rc == LPF_OK; ++g)
-        if (cudaEventCreateWithFlags(&s->ev_dd[g], cudaEventDisableTiming) != cudaSuccess) rc = LPF_E_CUDA;
-    if (rc == LPF_OK && cudaEventCreateWithFlags(&s->ev_b_done, cudaEventDisableTiming) != cudaSuccess) rc = LPF_E_CUDA;
     if (rc == LPF_OK && cudaFuncSetAttribute(lpf::k_filter<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)filter_smem_bytes(8, 8)) != cudaSuccess) rc = LPF_E_CUDA;
     if (rc == LPF_OK && cudaFuncSetAttribute(lpf::k_filter<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -695,7 +646,7 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
             rc = LPF_E_CUDA;
     }
     for (int k = 0; k < s->n_slots && rc == LPF_OK; ++k)
-        for (int i = 0; i < 2 * kProfPairs && rc == LPF_OK; ++i)
+        for (int i = 0; i <= ST_N && rc == LPF_OK; ++i)
             if (cudaEventCreate(&s->ev[k][i]) != cudaSuccess) rc = LPF_E_CUDA;
     if (rc == LPF_OK) {
         if (cudaMallocHost(&s->h_count, sizeof(unsigned) * kMaxSlots) != cudaSuccess ||
@@ -866,7 +817,6 @@ int lpf_stream_info(const lpf_stream* s, lpf_stream_info_t* out) {
 int lpf_stream_sync(lpf_stream* s) {
     if (!s) return LPF_E_ARG;
     if (cudaSetDevice(s->dev) != cudaSuccess) return LPF_E_CUDA;
-    if (cudaStreamSynchronize(s->st_b) != cudaSuccess) return LPF_E_CUDA;
     return cuda_fail(cudaStreamSynchronize(s->st));
 }
 
