@@ -58,6 +58,32 @@ def workload_spec(dtype):
     return synth.spec_aartfaac(dtype=dtype)
 
 
+# Minimal FP32 work of the filter per pixel and distinct trial, given D - C: square,
+# horizontal and vertical sliding sums (add + subtract each), normalise, rsqrt,
+# multiply (S/N), threshold compare, two statistics accumulations.
+FILTER_OPS_PER_PIXEL_TRIAL = 11
+
+
+def kernel_traffic():
+    """DRAM bytes per launch from the committed ncu capture, or None where the kernel's
+    source has changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return {}
+    out = {}
+    for k, v in rec.items():
+        src = os.path.join(ROOT, v["source"])
+        try:
+            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        except Exception:
+            continue
+        out[k] = v["dram_bytes_per_launch"] if sha == v["sha256"] else None
+    return out
+
+
 def algorithmic_bytes(spec, delays, n_distinct):
     """Bytes a push must move at minimum, per stage, with storage type of b bytes."""
     b = 4 if spec.dtype == "fp32" else 2
@@ -88,7 +114,7 @@ class Clocks:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -269,24 +295,39 @@ def run_ours(args):
 
     if rank != 0:
         return
-    # dominant kernel and its roofline
+    # per-kernel rooflines from the CUDA-event stage times (on the launching stream)
     names = list(ktimes)
-    dom = max(names, key=lambda n: ktimes[n][0])
-    dom_ms = ktimes[dom][0] / max(ktimes[dom][1], 1)
+    per_push = {n: ktimes[n][0] / max(ktimes[n][1], 1) for n in names}
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    alg = nbytes.get(dom)
-    roof = None
-    if alg is not None:
-        ach = alg / (dom_ms / 1e3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": None, "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": alg, "avg_launch_ms": dom_ms}
+    peak_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = peaks.get("sm_max_mhz", 2032.0)
+    alu_peak = sms * 128 * sm_mhz * 1e6 / 1e12          # one FP32 op per lane per clock
+    traffic = kernel_traffic()
+    HW = spec.H * spec.W
+    nd = info["n_distinct"]
+    n_dd = 2                                              # raw ring -> D, residual ring -> D - C
+    dd_ms = per_push["dedisperse"] / n_dd
+    dd_bytes = nbytes["dedisperse"]
+    dd_ach = dd_bytes / (dd_ms / 1e3) / 1e9
+    f_ms = per_push["filter_detect"]
+    f_ops = FILTER_OPS_PER_PIXEL_TRIAL * HW * nd
+    f_ach = f_ops / (f_ms / 1e3) / 1e12
+    roof_dd = {"kernel": "k_dedisperse (shift-sum)", "bound": "hbm", "achieved": dd_ach, "peak": hbm_peak,
+               "unit": "GB/s", "frac": dd_ach / hbm_peak, "peak_source": peak_src,
+               "traffic": traffic.get("k_dedisperse_" + args.dtype),
+               "algorithmic_bytes_per_launch": dd_bytes, "avg_launch_ms": dd_ms, "launches_per_step": n_dd}
+    roof_f = {"kernel": "k_filter_res<15> (box spread, S/N, 3x3 maximum, stats)", "bound": "alu",
+              "achieved": f_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": f_ach / alu_peak,
+              "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
+              "traffic": traffic.get("k_filter_res"),
+              "algorithmic_flop_per_launch": f_ops, "avg_launch_ms": f_ms, "launches_per_step": 1}
+    roof = roof_f if f_ms >= dd_ms else roof_dd
     path_ach = nbytes["path"] / (elapsed / args.steps) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
@@ -304,14 +345,16 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(np.mean(e2e_cands) * 24 + spec.n_dm * 16)},
         "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
                        "p99": 1e3 * float(np.percentile(lat, 99)), "what": "push_frame_host -> poll"},
-        # per push: ingest, counter reset, shift-sum, filter, 3 per sort pass, format, stats
-        "gpu_launches": int(args.steps * (6 + 3 * _passes(spec))),
+        # per push: ingest + residual, counter reset, 2 shift-sums, filter, 3 per sort pass,
+        # format, stats
+        "gpu_launches": int(args.steps * (8 + 3 * _passes(spec))),
         "roofline": roof,
+        "rooflines": [roof_f, roof_dd],
         "path_roofline": {"bound": "hbm", "achieved": path_ach, "peak": hbm_peak, "unit": "GB/s",
                           "frac": path_ach / hbm_peak,
                           "algorithmic_bytes_per_step": nbytes["path"],
                           "note": "sum over subbands of distinct delay planes read once + ingest"},
-        "kernel_ms_per_step": {n: ktimes[n][0] / max(ktimes[n][1], 1) for n in names},
+        "kernel_ms_per_step": per_push,
         "candidates_per_step": ncand,
         "clocks": clk,
     }
