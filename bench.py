@@ -152,7 +152,7 @@ def oracle_sample(spec, frame_at, T, delays, dms):
     return time.perf_counter() - t
 
 
-def cpu_baseline(spec, st, delays, n_dm=12):
+def cpu_baseline(spec, st, delays, n_dm=36):
     """The FP64 oracle (as it stands, one process) on a bounded sample of one push."""
     import functools
     fa = functools.lru_cache(maxsize=64)(lambda t: st.frame(t).astype(np.float64))

@@ -8,6 +8,7 @@
 // and records an event; poll waits on that event with a deadline.
 #include "../../include/lpf.h"
 #include "lpf_kernels.cuh"
+#include "lpf_dedisperse.cuh"
 #include "lpf_residual.cuh"
 
 #include <algorithm>
@@ -25,7 +26,7 @@
 namespace {
 
 constexpr double kCdmSeconds = 4.148808e3;   // s MHz^2 cm^3 / pc (Sec. 3.2)
-constexpr int kSortBlocks = 148;
+using lpf::kSortBlocks;
 constexpr int kMaxSlots = 16;
 
 enum Stage { ST_INGEST, ST_DEDISP, ST_FILTER, ST_SORT, ST_FORMAT, ST_STATS, ST_N };
