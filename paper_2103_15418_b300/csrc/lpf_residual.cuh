@@ -29,6 +29,7 @@ struct ResGeom {
     static constexpr int RR = (TX + NR - 1) / NR;
     static constexpr int NT = 160;
     static_assert(WD <= NT, "one thread per loaded column");
+    static_assert(NT - TX == 32, "one copy warp beside the column warps");
 };
 
 // ---------------------------------------------------------------------------
@@ -158,16 +159,19 @@ __device__ __noinline__ void emit_res_candidates(const ResArgs& ra, int row, int
 
 // ---------------------------------------------------------------------------
 // k_filter_res: per distinct row (blockIdx.y) and 128-column strip, streaming
-// down in blocks of B rows with a triple buffer of R rows (cp.async prefetch of
-// block k+1 while block k is processed; block k-1 still holds the lagged rows):
-//   2. horizontal window sums of R^2 (two stacks)                -> hE
-//   3. per column: vertical window sum as the suffix of the previous (2r+1)-row
-//      segment plus the prefix of the current one (exact) -> S(ys), ys = row - r;
-//      snr = R(ys)/sqrt(S), stats, threshold, candidates.
+// down in blocks of B rows of R = D - C held in a triple buffer (block k, block
+// k-1 for the lagged rows, block k+1 being copied in):
+//   2. all warps: horizontal window sums of R^2 (two stacks)             -> hE
+//   3. warps 0-3, one column each: vertical window sum as the suffix of the
+//      previous (2r+1)-row segment plus the prefix of the current one (exact)
+//      -> S(ys), ys = row - r; snr = R(ys)/sqrt(S), stats; the snr is parked in
+//      the consumed hE slot and candidates are resolved once per block.
+//      warp 4 meanwhile issues the cp.async copies of block k+1.
 template <int R>
 __global__ void __launch_bounds__(ResGeom<R>::NT, 3) k_filter_res(ResArgs ra) {
     using G = ResGeom<R>;
     constexpr int TX = G::TX, B = G::B, L = G::L, SD = G::SD, SX = G::SX, WD = G::WD, NT = G::NT;
+    constexpr int NP = G::NP;
     extern __shared__ float sm[];
     float* Rb = sm;                     // [3][B][SD] R rows; col = x - (x0 - r)
     float* hE = Rb + 3 * B * SD;        // [B][SX]
@@ -179,6 +183,7 @@ __global__ void __launch_bounds__(ResGeom<R>::NT, 3) k_filter_res(ResArgs ra) {
     const float* Rimg = a.D + (int64_t)row * a.P;
     const int t = threadIdx.x;
     const int lane = t & 31;
+    const bool loader = t >= TX;        // warp 4: copies
     const int xs = x0 + t;
     const bool col_s = t < TX && xs < W;
     const int nx = col_s ? min(xs + R, W - 1) - max(xs - R, 0) + 1 : 0;
@@ -190,31 +195,31 @@ __global__ void __launch_bounds__(ResGeom<R>::NT, 3) k_filter_res(ResArgs ra) {
     double d1 = 0.0, d2 = 0.0, dc = 0.0;
     const int m0 = a.member_start[row], nm = a.member_start[row + 1] - m0;
 
-    auto load = [&](int kk) {
-        if (t >= WD) return;
-        float* dst = Rb + (kk % 3) * B * SD + t;
-        const int x = x0 - R + t;
-        const bool colok = x >= 0 && x < W;
+    // copies of block kk (rows kk*B ..) by the threads of [t0, t0 + nthr)
+    auto load = [&](int kk, int t0, int nthr) {
+        float* dst = Rb + (kk % 3) * B * SD;
         const int yb = kk * B;
-        const float* src = Rimg + (int64_t)yb * W + x;
-#pragma unroll
-        for (int j = 0; j < B; ++j) {
-            bool in = colok && yb + j < H;
-            cp_async4(dst + j * SD, in ? src : Rimg, in);
-            src += W;
+        for (int c = t - t0; c < WD; c += nthr) {
+            const int x = x0 - R + c;
+            const bool colok = x >= 0 && x < W;
+            const float* src = Rimg + (int64_t)yb * W + x;
+#pragma unroll 4
+            for (int j = 0; j < B; ++j) {
+                bool in = colok && yb + j < H;
+                cp_async4(dst + j * SD + c, in ? src : Rimg, in);
+                src += W;
+            }
         }
     };
     const int nblk = (H + R + B - 1) / B;
-    load(0);
+    load(0, 0, NT);
     cp_async_commit();
     for (int k = 0; k < nblk; ++k) {
         const int ybase = k * B;
         const float* cur = Rb + (k % 3) * B * SD;
         const float* prev = Rb + ((k + 2) % 3) * B * SD;
-        if (k + 1 < nblk) load(k + 1);
-        cp_async_commit();
         if (t < B) rowS[t] = row_count<R>(ybase + t - R, H);
-        asm volatile("cp.async.wait_group 1;\n" ::);
+        asm volatile("cp.async.wait_group 0;\n" ::);
         __syncthreads();
         // ---- horizontal window sums of R^2 over buffer cols c .. c + 2r (output col x0 + c)
         for (int it = t; it < B * G::NR; it += NT) {
@@ -227,40 +232,53 @@ __global__ void __launch_bounds__(ResGeom<R>::NT, 3) k_filter_res(ResArgs ra) {
                                     [&](int c, float v) { out[c] = v; });
         }
         __syncthreads();
-        // ---- vertical segment sums -> S for row ys = ybase + j - r; detect
-        {
+        if (loader) {
+            // ---- the next block's copies while the column warps run the vertical pass
+            if (k + 1 < nblk) load(k + 1, TX, NT - TX);
+            cp_async_commit();
+        } else {
+            // ---- vertical segment sums -> S for row ys = ybase + j - r; snr parked in hE
             float s1 = 0.f, s2 = 0.f, cnt = 0.f;
+            unsigned cm = 0;
 #pragma unroll
-            for (int j = 0; j < B; ++j) {
-                const int o = j % L;
-                const float in = col_s ? hE[j * SX + t] : 0.f;
-                raw[o] = in;
-                pre = (o == 0) ? in : pre + in;
-                const float Ssum = (o + 1 < L) ? suf[o + 1] + pre : pre;
-                if (o == L - 1) {
-                    float acc = 0.f;
+            for (int sgm = 0; sgm < NP; ++sgm) {
 #pragma unroll
-                    for (int i = L - 1; i >= 1; --i) { acc += raw[i]; suf[i] = acc; }
-                }
-                const int ys = ybase + j - R;
-                const float2 sy = rowS[j];
-                const float S = Ssum * (sy.y * inv_nx);
-                const bool valid = col_s && sy.x > 0.f && S > 0.f;
-                float snr = 0.f;
-                if (valid) {
+                for (int o = 0; o < L; ++o) raw[o] = col_s ? hE[(sgm * L + o) * SX + t] : 0.f;
+#pragma unroll
+                for (int o = 0; o < L; ++o) {
+                    const int j = sgm * L + o;
+                    pre = (o == 0) ? raw[0] : pre + raw[o];
+                    const float Ssum = (o + 1 < L) ? suf[o + 1] + pre : pre;
+                    const float2 sy = rowS[j];
+                    const float S = Ssum * (sy.y * inv_nx);
+                    const bool valid = col_s && sy.x > 0.f && S > 0.f;
                     const float rv = (j >= R) ? cur[(j - R) * SD + t + R] : prev[(B + j - R) * SD + t + R];
-                    snr = rv * rsqrtf(S);
-                    s1 += snr;
-                    s2 = fmaf(snr, snr, s2);
-                    cnt += 1.f;
+                    float snr = 0.f;
+                    if (valid) {
+                        snr = rv * rsqrtf(S);
+                        s1 += snr;
+                        s2 = fmaf(snr, snr, s2);
+                        cnt += 1.f;
+                    }
+                    if (valid && snr > a.kappa) cm |= 1u << j;
+                    if (t < TX) hE[j * SX + t] = snr;
                 }
-                const bool cand = valid && snr > a.kappa;
-                if (__any_sync(0xffffffffu, cand))
-                    emit_res_candidates(ra, row, ys, xs, snr, cand, m0, nm);
+                // suffix sums of the finished segment for the next one
+                float acc = 0.f;
+#pragma unroll
+                for (int i = L - 1; i >= 1; --i) { acc += raw[i]; suf[i] = acc; }
             }
             d1 += s1;
             d2 += s2;
             dc += cnt;
+            // ---- candidates of this block (rare): rows with a set bit anywhere in the warp
+            unsigned any = __reduce_or_sync(0xffffffffu, cm);
+            while (any) {
+                const int j = __ffs(any) - 1;
+                any &= any - 1;
+                const bool cand = (cm >> j) & 1u;
+                emit_res_candidates(ra, row, ybase + j - R, xs, cand ? hE[j * SX + t] : 0.f, cand, m0, nm);
+            }
         }
         __syncthreads();
     }
