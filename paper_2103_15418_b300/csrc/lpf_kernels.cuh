@@ -352,34 +352,66 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint64_t* __rest
 }
 
 // Exclusive scan of hist[256 * nb] (digit-major), one block of 1024 threads:
-// each thread loads its contiguous chunk at once, the chunk sums are scanned in
-// shared memory, and every entry gets its chunk's offset plus its local prefix.
-constexpr int kScanPer = (256 * kSortBlocks + 1023) / 1024;
+// warp w owns digits 8w .. 8w+7; it loads their nb block counts at once
+// (coalesced, nb <= 160), scans each digit with warp shuffles, and after the
+// 256 digit totals are scanned adds the digit offset on the way back.
+static_assert(kSortBlocks <= 160, "scan holds 5 chunks of 32 block counts per digit");
 __global__ void __launch_bounds__(1024) k_rs_scan(unsigned* __restrict__ hist, int nb) {
-    __shared__ unsigned part[1024];
-    const int total = 256 * nb;
-    const int lo = threadIdx.x * kScanPer;
-    unsigned v[kScanPer];
-    unsigned s = 0;
+    __shared__ unsigned tot[256];
+    __shared__ unsigned base[256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
-        v[k] = (lo + k < total) ? hist[lo + k] : 0u;
-        s += v[k];
+    for (int half = 0; half < 2; ++half) {
+        unsigned v[4][5];
+#pragma unroll
+        for (int dd = 0; dd < 4; ++dd)
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                const int i = c * 32 + lane;
+                v[dd][c] = i < nb ? hist[(warp * 8 + 4 * half + dd) * nb + i] : 0u;
+            }
+#pragma unroll
+        for (int dd = 0; dd < 4; ++dd) {
+            const int d = warp * 8 + 4 * half + dd;
+            unsigned run = 0;
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                unsigned inc = v[dd][c];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    unsigned u = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += u;
+                }
+                const int i = c * 32 + lane;
+                if (i < nb) hist[d * nb + i] = run + inc - v[dd][c];
+                run += __shfl_sync(0xffffffffu, inc, 31);
+            }
+            if (lane == 0) tot[d] = run;
+        }
     }
-    part[threadIdx.x] = s;
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        unsigned u = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += u;
-        __syncthreads();
-    }
-    unsigned run = part[threadIdx.x] - s;
+    if (warp == 0) {
+        unsigned w8[8], sum = 0;
 #pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
-        if (lo + k < total) hist[lo + k] = run;
-        run += v[k];
+        for (int k = 0; k < 8; ++k) { w8[k] = tot[lane * 8 + k]; sum += w8[k]; }
+        unsigned inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        unsigned run = inc - sum;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { base[lane * 8 + k] = run; run += w8[k]; }
     }
+    __syncthreads();
+#pragma unroll
+    for (int dd = 0; dd < 8; ++dd)
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            const int i = c * 32 + lane;
+            if (i < nb) hist[(warp * 8 + dd) * nb + i] += base[warp * 8 + dd];
+        }
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(
