@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pool", type=int, default=12, help="distinct synthetic frames cycled")
+    ap.add_argument("--workload", default="aartfaac", choices=["aartfaac", "serving"],
+                    help="serving: four concurrent FP16 streams through the C++ serving loop")
+    ap.add_argument("--cadence", type=float, default=1.0, help="serving: frame cadence in seconds")
+    ap.add_argument("--frames", type=int, default=60, help="serving: frames per stream")
     return ap.parse_args()
 
 
@@ -368,8 +372,64 @@ def _passes(spec):
     return (bits(spec.W) + bits(spec.H) + bits(spec.n_dm) + 7) // 8
 
 
+def run_serving(args):
+    """Serving mix: 2048^2/16/501, 1024^2/16/251 and 2 x 512^2/8/128 FP16 streams, frames
+    submitted at the cadence with +-5% jitter; p50/p99 submit -> finish latency and the
+    aggregate pixel*DM-trials/s of the finished frames."""
+    import threading
+    import torch
+    import paper_2103_15418_b300 as lpf
+    specs = synth.spec_serving_mix()
+    pools = []
+    for i, sp in enumerate(specs):
+        st = synth.SyntheticStream(sp, seed=60 + i)
+        pools.append([st.frame(t) for t in range(4)])
+    budget = 80 << 30
+    n = args.frames
+    jit = np.random.default_rng(7)
+    with lpf.Server(budget, max_streams=8) as srv:
+        ids = [srv.open_stream(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth, kappa=sp.kappa,
+                               box_r=sp.box_r, dtype=sp.dtype) for sp in specs]
+        counts = {i: 0 for i in ids}
+
+        def drain(i):
+            while counts[i] < n:
+                srv.fetch(i, timeout_ms=600000)
+                counts[i] += 1
+        threads = [threading.Thread(target=drain, args=(i,)) for i in ids]
+        for th in threads:
+            th.start()
+        t0 = time.perf_counter()
+        # staggered, jittered arrivals: stream k's frame T is due at (T + k/4) * cadence +- 5%
+        events = sorted((T + k / len(ids) + jit.uniform(-0.05, 0.05)) * args.cadence for T in range(n)
+                        for k in range(len(ids)))
+        order = sorted(((T + k / len(ids)) * args.cadence, k, T) for T in range(n) for k in range(len(ids)))
+        for (due, k, T), ev in zip(order, events):
+            wait = t0 + ev - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            while srv.submit(ids[k], pools[k][T % 4], T) == lpf.LPF_E_BUSY:
+                time.sleep(0.0005)
+        for th in threads:
+            th.join()
+        wall = time.perf_counter() - t0
+        stats = srv.stats()
+        per = {specs[i].name: srv.stats(ids[i]) for i in range(len(ids))}
+    pixdm = sum(sp.H * sp.W * sp.n_dm for sp in specs) * n
+    line = {"metric": METRIC, "workload": "serving-mix-4-streams-fp16", "cadence_s": args.cadence,
+            "frames_per_stream": n, "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"],
+            "max_ms": stats["max_ms"], "pixel_dm_per_s_served": stats["pixel_dm_per_s"],
+            "offered_pixel_dm_per_s": pixdm / wall,
+            "per_stream_p99_ms": {k: v["p99_ms"] for k, v in per.items()},
+            "hbm_budget_bytes": budget, "peak_used_bytes": stats["used_bytes"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "serving":
+        run_serving(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
