@@ -51,6 +51,16 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """Largest value over all ranks (the slowest rank's time); identity without a process group."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -269,10 +279,7 @@ def run_ours(args):
     s.set_profiling(False)
     elapsed = ev0.elapsed_time(ev1) / 1e3
     ktimes = s.kernel_times(reset=True)
-    if dist is not None:
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, dist, dev)
     ncand = float(np.mean(polled[-args.steps:]))
     pix_dm = spec.H * spec.W * spec.n_dm
     value = pix_dm * args.steps * ws / elapsed
@@ -290,10 +297,7 @@ def run_ours(args):
         e2e_cands.append(n)
         lat.append(time.perf_counter() - t0)
     e2e_s = time.perf_counter() - t_e0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist, dev)
     e2e_value = pix_dm * args.e2e_steps * ws / e2e_s
     s.close()
 
