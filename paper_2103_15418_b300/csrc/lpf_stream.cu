@@ -209,6 +209,27 @@ void build_plan(lpf_stream* s) {
         if (da != db) return da < db;
         return groups[a][0] < groups[b][0];
     });
+    // Inside each run of equal largest delay (any order there keeps the rows of
+    // a warm-up prefix), order the rows greedily so that consecutive rows differ
+    // in as few subbands as possible: the shift-sum reloads only those planes.
+    auto lag_of = [&](int g, int f) { int d = groups[g][0]; return s->dmax[d] - s->delay[(size_t)d * s->F + f]; };
+    for (size_t a = 0; a < order.size();) {
+        size_t b = a;
+        while (b < order.size() && s->dmax[groups[order[b]][0]] == s->dmax[groups[order[a]][0]]) ++b;
+        for (size_t i = a; i < b && b - a <= 4096; ++i) {
+            if (i == 0) continue;
+            const int prev = order[i - 1];
+            size_t best = i;
+            int best_cost = s->F + 1;
+            for (size_t j = i; j < b; ++j) {
+                int c = 0;
+                for (int f = 0; f < s->F; ++f) c += lag_of(order[j], f) != lag_of(prev, f);
+                if (c < best_cost || (c == best_cost && order[j] < order[best])) { best_cost = c; best = j; }
+            }
+            std::swap(order[i], order[best]);
+        }
+        a = b;
+    }
     s->n_distinct = (int)groups.size();
     // canonical trial ranks
     std::vector<int> tr(s->n_dm);
@@ -291,26 +312,31 @@ int set_res_attributes() {
 // split into two segments (each restarts its register state) for parallelism.
 template <typename TS>
 void launch_dedisperse_ring(lpf_stream* s, const void* ring_v, float* out, int n_rows, int Tmod) {
-    const int nseg = n_rows >= 32 ? 2 : 1;
+    // two row segments (more where one segment's plane table would exceed 48 KB of shared memory)
+    int nseg = n_rows >= 32 ? 2 : 1;
+    while (lpf::dedisperse_smem_bytes((n_rows + nseg - 1) / nseg, s->F) > 48 * 1024) ++nseg;
     const int seg = (n_rows + nseg - 1) / nseg;
+    const size_t smem = lpf::dedisperse_smem_bytes(seg, s->F);
+    const int F = s->F;
+    auto go = [&](auto kern, int px) {
+        dim3 grid((unsigned)((s->P / px + 255) / 256), (unsigned)nseg);
+        kern<<<grid, 256, smem, s->st>>>(reinterpret_cast<const TS*>(ring_v), out, s->d_lag, s->d_chg, F,
+                                         s->depth, Tmod, n_rows, seg, s->P);
+    };
     if constexpr (sizeof(TS) == 4) {
-        const float* ring = reinterpret_cast<const float*>(ring_v);
-        dim3 grid((unsigned)((s->P / 4 + 255) / 256), (unsigned)nseg);
-        if (s->F <= 8)
-            lpf::k_dedisperse<8><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, seg, s->P);
-        else if (s->F <= 16)
-            lpf::k_dedisperse<16><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, seg, s->P);
-        else
-            lpf::k_dedisperse<32><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, seg, s->P);
+        if (F == 8) go(lpf::k_dedisperse<8, true>, 4);
+        else if (F == 16) go(lpf::k_dedisperse<16, true>, 4);
+        else if (F == 32) go(lpf::k_dedisperse<32, true>, 4);
+        else if (F < 8) go(lpf::k_dedisperse<8, false>, 4);
+        else if (F < 16) go(lpf::k_dedisperse<16, false>, 4);
+        else go(lpf::k_dedisperse<32, false>, 4);
     } else {
-        const TS* ring = reinterpret_cast<const TS*>(ring_v);
-        dim3 grid((unsigned)((s->P / 8 + 255) / 256), (unsigned)nseg);
-        if (s->F <= 8)
-            lpf::k_dedisperse16<8, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, seg, s->P);
-        else if (s->F <= 16)
-            lpf::k_dedisperse16<16, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, seg, s->P);
-        else
-            lpf::k_dedisperse16<32, TS><<<grid, 256, 0, s->st>>>(ring, out, s->d_lag, s->d_chg, s->F, s->depth, Tmod, n_rows, seg, s->P);
+        if (F == 8) go(lpf::k_dedisperse16<8, true, TS>, 8);
+        else if (F == 16) go(lpf::k_dedisperse16<16, true, TS>, 8);
+        else if (F == 32) go(lpf::k_dedisperse16<32, true, TS>, 8);
+        else if (F < 8) go(lpf::k_dedisperse16<8, false, TS>, 8);
+        else if (F < 16) go(lpf::k_dedisperse16<16, false, TS>, 8);
+        else go(lpf::k_dedisperse16<32, false, TS>, 8);
     }
 }
 
