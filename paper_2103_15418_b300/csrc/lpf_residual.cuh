@@ -37,11 +37,13 @@ struct ResGeom {
 // mean of radius R (horizontal two-stack sums, vertical sliding sum, C by
 // reciprocal plus one Newton step against the exact count, so a constant
 // window gives Xr = 0 exactly).  X is read as stored (storage type TS) and Xr
-// is written in the storage type.  Grid: (strips, F).
+// is written in the storage type.  Grid: (strips, F, row segments); a segment
+// of seg_rows output rows streams from r rows above it (its vertical window
+// starts there) to r rows below it.
 template <int R, typename TS>
 __global__ void __launch_bounds__(ResGeom<R>::NT) k_residual(const TS* __restrict__ raw_slot,
                                                              TS* __restrict__ res_slot, int H, int W,
-                                                             int64_t P) {
+                                                             int64_t P, int seg_rows) {
     using G = ResGeom<R>;
     constexpr int TX = G::TX, B = G::B, L = G::L, SD = G::SD, SX = G::SX, WD = G::WD;
     extern __shared__ float smr[];
@@ -63,9 +65,11 @@ __global__ void __launch_bounds__(ResGeom<R>::NT) k_residual(const TS* __restric
 #pragma unroll
     for (int i = 0; i < L; ++i) hist[i] = 0.f;
     float v = 0.f;
-    const int nblk = (H + R + B - 1) / B;
+    const int y0 = blockIdx.z * seg_rows, y1 = min(H, y0 + seg_rows);
+    const int ys0 = max(0, y0 - R);             // first input row
+    const int nblk = (y1 + R - ys0 + B - 1) / B;
     for (int k = 0; k < nblk; ++k) {
-        const int ybase = k * B;
+        const int ybase = ys0 + k * B;
         float(*cur)[SD] = Xb[k & 1];
         float(*prev)[SD] = Xb[(k + 1) & 1];
         if (t < WD) {
@@ -98,7 +102,7 @@ __global__ void __launch_bounds__(ResGeom<R>::NT) k_residual(const TS* __restric
                 const int yc = ybase + j - R;
                 const float2 cy = rowC[j];
                 const float n = cy.x * nxf, inv = cy.y * inv_nx;
-                if (n > 0.f) {
+                if (n > 0.f && yc >= y0 && yc < y1) {
                     const float c0 = v * inv;
                     const float C = fmaf(fmaf(-c0, n, v), inv, c0);
                     const float xv = (j >= R) ? cur[j - R][t + R] : prev[B + j - R][t + R];
@@ -159,22 +163,27 @@ __device__ __noinline__ void emit_res_candidates(const ResArgs& ra, int row, int
 
 // ---------------------------------------------------------------------------
 // k_filter_res: per distinct row (blockIdx.y) and 128-column strip, streaming
-// down in blocks of B rows of R = D - C held in a triple buffer (block k, block
-// k-1 for the lagged rows, block k+1 being copied in):
-//   2. all warps: horizontal window sums of R^2 (two stacks)             -> hE
+// down in blocks of B rows of R = D - C held in a double buffer (block k being
+// used, block k+1 being copied in):
+//   2. all warps: horizontal window sums of R^2 (two stacks), warp w one run of
+//      columns, lane = row                                               -> hE
 //   3. warps 0-3, one column each: vertical window sum as the suffix of the
 //      previous (2r+1)-row segment plus the prefix of the current one (exact)
 //      -> S(ys), ys = row - r; snr = R(ys)/sqrt(S), stats; the snr is parked in
-//      the consumed hE slot and candidates are resolved once per block.
+//      the consumed hE slot and candidates are resolved once per block.  R(ys)
+//      of the first r rows lies in block k-1, whose buffer is being refilled:
+//      it is read from global memory (L2; the block was copied one step ago).
 //      warp 4 meanwhile issues the cp.async copies of block k+1.
 template <int R>
-__global__ void __launch_bounds__(ResGeom<R>::NT, 3) k_filter_res(ResArgs ra) {
+__global__ void __launch_bounds__(ResGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
     using G = ResGeom<R>;
     constexpr int TX = G::TX, B = G::B, L = G::L, SD = G::SD, SX = G::SX, WD = G::WD, NT = G::NT;
-    constexpr int NP = G::NP;
+    constexpr int NP = G::NP, RR = G::RR, NR = G::NR;
+    constexpr int LAST = TX - (NR - 1) * RR;         // columns of the last run
+    static_assert(B <= 32 && LAST > 0 && LAST <= RR, "lane = row; ragged last run");
     extern __shared__ float sm[];
-    float* Rb = sm;                     // [3][B][SD] R rows; col = x - (x0 - r)
-    float* hE = Rb + 3 * B * SD;        // [B][SX]
+    float* Rb = sm;                     // [2][B][SD] R rows; col = x - (x0 - r)
+    float* hE = Rb + 2 * B * SD;        // [B][SX]
     __shared__ float2 rowS[B];
     const FilterArgs& a = ra.a;
     const int strip = blockIdx.x, row = blockIdx.y;
@@ -182,12 +191,13 @@ __global__ void __launch_bounds__(ResGeom<R>::NT, 3) k_filter_res(ResArgs ra) {
     const int H = a.H, W = a.W;
     const float* Rimg = a.D + (int64_t)row * a.P;
     const int t = threadIdx.x;
-    const int lane = t & 31;
+    const int lane = t & 31, warp = t >> 5;
     const bool loader = t >= TX;        // warp 4: copies
     const int xs = x0 + t;
     const bool col_s = t < TX && xs < W;
     const int nx = col_s ? min(xs + R, W - 1) - max(xs - R, 0) + 1 : 0;
     const float inv_nx = col_s ? 1.0f / (float)nx : 0.f;
+    const bool interior = x0 - R >= 0 && x0 - R + WD <= W;
     float raw[L], suf[L];
 #pragma unroll
     for (int i = 0; i < L; ++i) { raw[i] = 0.f; suf[i] = 0.f; }
@@ -197,17 +207,25 @@ __global__ void __launch_bounds__(ResGeom<R>::NT, 3) k_filter_res(ResArgs ra) {
 
     // copies of block kk (rows kk*B ..) by the threads of [t0, t0 + nthr)
     auto load = [&](int kk, int t0, int nthr) {
-        float* dst = Rb + (kk % 3) * B * SD;
+        float* dst = Rb + (kk & 1) * B * SD;
         const int yb = kk * B;
-        for (int c = t - t0; c < WD; c += nthr) {
-            const int x = x0 - R + c;
-            const bool colok = x >= 0 && x < W;
-            const float* src = Rimg + (int64_t)yb * W + x;
+        if (interior && yb + B <= H) {
+            for (int c = t - t0; c < WD; c += nthr) {
+                const float* src = Rimg + (int64_t)yb * W + (x0 - R + c);
+#pragma unroll
+                for (int j = 0; j < B; ++j) cp_async4(dst + j * SD + c, src + (int64_t)j * W, true);
+            }
+        } else {
+            for (int c = t - t0; c < WD; c += nthr) {
+                const int x = x0 - R + c;
+                const bool colok = x >= 0 && x < W;
+                const float* src = Rimg + (int64_t)yb * W + x;
 #pragma unroll 4
-            for (int j = 0; j < B; ++j) {
-                bool in = colok && yb + j < H;
-                cp_async4(dst + j * SD + c, in ? src : Rimg, in);
-                src += W;
+                for (int j = 0; j < B; ++j) {
+                    bool in = colok && yb + j < H;
+                    cp_async4(dst + j * SD + c, in ? src : Rimg, in);
+                    src += W;
+                }
             }
         }
     };
@@ -216,20 +234,20 @@ __global__ void __launch_bounds__(ResGeom<R>::NT, 3) k_filter_res(ResArgs ra) {
     cp_async_commit();
     for (int k = 0; k < nblk; ++k) {
         const int ybase = k * B;
-        const float* cur = Rb + (k % 3) * B * SD;
-        const float* prev = Rb + ((k + 2) % 3) * B * SD;
+        const float* cur = Rb + (k & 1) * B * SD;
         if (t < B) rowS[t] = row_count<R>(ybase + t - R, H);
         asm volatile("cp.async.wait_group 0;\n" ::);
         __syncthreads();
         // ---- horizontal window sums of R^2 over buffer cols c .. c + 2r (output col x0 + c)
-        for (int it = t; it < B * G::NR; it += NT) {
-            int j = it % B, run = it / B;
-            int c0 = run * G::RR;
-            int len = min(G::RR, TX - c0);
-            const float* in = cur + j * SD;
-            float* out = hE + j * SX;
-            two_stack_run<R, G::RR>(c0, len, [&](int c) { float r = in[c]; return r * r; },
-                                    [&](int c, float v) { out[c] = v; });
+        for (int ru = warp; ru < NR; ru += NT / 32) {
+            if (lane < B) {
+                const float* in = cur + lane * SD;
+                float* out = hE + lane * SX;
+                auto ld = [&](int c) { float r = in[c]; return r * r; };
+                auto st = [&](int c, float v) { out[c] = v; };
+                if (ru < NR - 1) two_stack_run<R, RR>(ru * RR, RR, ld, st);
+                else two_stack_run<R, LAST>((NR - 1) * RR, LAST, ld, st);
+            }
         }
         __syncthreads();
         if (loader) {
@@ -237,6 +255,13 @@ __global__ void __launch_bounds__(ResGeom<R>::NT, 3) k_filter_res(ResArgs ra) {
             if (k + 1 < nblk) load(k + 1, TX, NT - TX);
             cp_async_commit();
         } else {
+            // R(ys) of the rows of block k-1 (ys = ybase - r .. ybase - 1)
+            float rvp[R];
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const int ys = ybase + j - R;
+                rvp[j] = (col_s && ys >= 0 && ys < H) ? __ldg(Rimg + (int64_t)ys * W + xs) : 0.f;
+            }
             // ---- vertical segment sums -> S for row ys = ybase + j - r; snr parked in hE
             float s1 = 0.f, s2 = 0.f, cnt = 0.f;
             unsigned cm = 0;
@@ -252,7 +277,7 @@ __global__ void __launch_bounds__(ResGeom<R>::NT, 3) k_filter_res(ResArgs ra) {
                     const float2 sy = rowS[j];
                     const float S = Ssum * (sy.y * inv_nx);
                     const bool valid = col_s && sy.x > 0.f && S > 0.f;
-                    const float rv = (j >= R) ? cur[(j - R) * SD + t + R] : prev[(B + j - R) * SD + t + R];
+                    const float rv = (j >= R) ? cur[(j - R) * SD + t + R] : rvp[j < R ? j : 0];
                     float snr = 0.f;
                     if (valid) {
                         snr = rv * rsqrtf(S);
@@ -261,7 +286,7 @@ __global__ void __launch_bounds__(ResGeom<R>::NT, 3) k_filter_res(ResArgs ra) {
                         cnt += 1.f;
                     }
                     if (valid && snr > a.kappa) cm |= 1u << j;
-                    if (t < TX) hE[j * SX + t] = snr;
+                    hE[j * SX + t] = snr;
                 }
                 // suffix sums of the finished segment for the next one
                 float acc = 0.f;
@@ -307,7 +332,7 @@ constexpr size_t residual_smem_bytes() {
 
 template <int R>
 constexpr size_t res_filter_smem_bytes() {
-    return ((size_t)3 * ResGeom<R>::B * ResGeom<R>::SD + (size_t)ResGeom<R>::B * ResGeom<R>::SX) * sizeof(float);
+    return ((size_t)2 * ResGeom<R>::B * ResGeom<R>::SD + (size_t)ResGeom<R>::B * ResGeom<R>::SX) * sizeof(float);
 }
 
 }  // namespace lpf

@@ -276,11 +276,19 @@ template <typename TS>
 void launch_residual(lpf_stream* s, int64_t slot) {
     const TS* raw = reinterpret_cast<const TS*>(s->ring) + slot * s->F * s->P;
     TS* res = reinterpret_cast<TS*>(s->resring) + slot * s->F * s->P;
-    dim3 grid((unsigned)s->n_strips, (unsigned)s->F);
+    // row segments so that about two waves of CTAs (4 per SM) run; a segment
+    // keeps at least 4 row blocks so that its 2r halo rows stay a small share
+    const int B = s->prm.box_r == 7 ? lpf::ResGeom<7>::B : lpf::ResGeom<15>::B;
+    const int per_plane = s->n_strips * s->F;
+    int nseg = std::max(1, (2 * 4 * 148 + per_plane - 1) / per_plane);
+    nseg = std::min(nseg, std::max(1, s->H / (4 * B)));
+    const int seg_rows = (s->H + nseg - 1) / nseg;
+    nseg = (s->H + seg_rows - 1) / seg_rows;
+    dim3 grid((unsigned)s->n_strips, (unsigned)s->F, (unsigned)nseg);
     if (s->prm.box_r == 7)
-        lpf::k_residual<7, TS><<<grid, lpf::ResGeom<7>::NT, lpf::residual_smem_bytes<7>(), s->st>>>(raw, res, s->H, s->W, s->P);
+        lpf::k_residual<7, TS><<<grid, lpf::ResGeom<7>::NT, lpf::residual_smem_bytes<7>(), s->st>>>(raw, res, s->H, s->W, s->P, seg_rows);
     else
-        lpf::k_residual<15, TS><<<grid, lpf::ResGeom<15>::NT, lpf::residual_smem_bytes<15>(), s->st>>>(raw, res, s->H, s->W, s->P);
+        lpf::k_residual<15, TS><<<grid, lpf::ResGeom<15>::NT, lpf::residual_smem_bytes<15>(), s->st>>>(raw, res, s->H, s->W, s->P, seg_rows);
 }
 
 void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows) {
