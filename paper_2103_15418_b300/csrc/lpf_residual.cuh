@@ -170,10 +170,13 @@ __device__ __noinline__ void emit_res_candidates(const ResArgs& ra, int row, int
 //   3. warps 0-3, one column each: vertical window sum as the suffix of the
 //      previous (2r+1)-row segment plus the prefix of the current one (exact)
 //      -> S(ys), ys = row - r; snr = R(ys)/sqrt(S), stats; the snr is parked in
-//      the consumed hE slot and candidates are resolved once per block.  R(ys)
+//      block k's R buffer and candidates are resolved once per block.  R(ys)
 //      of the first r rows lies in block k-1, whose buffer is being refilled:
 //      it is read from global memory (L2; the block was copied one step ago).
 //      warp 4 meanwhile issues the cp.async copies of block k+1.
+//   One barrier per block publishes the copies and separates the vertical pass
+//   of block k-1 from the horizontal pass of block k; a second one separates
+//   the horizontal and vertical passes of block k.
 template <int R>
 __global__ void __launch_bounds__(ResGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
     using G = ResGeom<R>;
@@ -198,9 +201,9 @@ __global__ void __launch_bounds__(ResGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
     const int nx = col_s ? min(xs + R, W - 1) - max(xs - R, 0) + 1 : 0;
     const float inv_nx = col_s ? 1.0f / (float)nx : 0.f;
     const bool interior = x0 - R >= 0 && x0 - R + WD <= W;
-    float raw[L], suf[L];
+    float suf[L];
 #pragma unroll
-    for (int i = 0; i < L; ++i) { raw[i] = 0.f; suf[i] = 0.f; }
+    for (int i = 0; i < L; ++i) suf[i] = 0.f;
     float pre = 0.f;
     double d1 = 0.0, d2 = 0.0, dc = 0.0;
     const int m0 = a.member_start[row], nm = a.member_start[row + 1] - m0;
@@ -235,9 +238,11 @@ __global__ void __launch_bounds__(ResGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
     for (int k = 0; k < nblk; ++k) {
         const int ybase = k * B;
         const float* cur = Rb + (k & 1) * B * SD;
-        if (t < B) rowS[t] = row_count<R>(ybase + t - R, H);
+        // one barrier both publishes the copies of block k and ends the vertical
+        // pass of block k-1 (its reads of hE and rowS)
         asm volatile("cp.async.wait_group 0;\n" ::);
         __syncthreads();
+        if (t < B) rowS[t] = row_count<R>(ybase + t - R, H);
         // ---- horizontal window sums of R^2 over buffer cols c .. c + 2r (output col x0 + c)
         for (int ru = warp; ru < NR; ru += NT / 32) {
             if (lane < B) {
@@ -255,43 +260,47 @@ __global__ void __launch_bounds__(ResGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
             if (k + 1 < nblk) load(k + 1, TX, NT - TX);
             cp_async_commit();
         } else {
-            // R(ys) of the rows of block k-1 (ys = ybase - r .. ybase - 1)
+            // R(ys) of the rows of block k-1 (ys = ybase - r .. ybase - 1), from
+            // global memory, loaded ahead of the pass
             float rvp[R];
 #pragma unroll
             for (int j = 0; j < R; ++j) {
                 const int ys = ybase + j - R;
                 rvp[j] = (col_s && ys >= 0 && ys < H) ? __ldg(Rimg + (int64_t)ys * W + xs) : 0.f;
             }
-            // ---- vertical segment sums -> S for row ys = ybase + j - r; snr parked in hE
+            // the snr of row j is parked in block k's buffer at row pk(j): the slot
+            // of its own centre value (j >= r, read just before) or one of the last
+            // r rows, which this pass does not read (the next pass reads them from
+            // global memory and the buffer is refilled only after the next barrier)
+            float* park = Rb + (k & 1) * B * SD + t + R;
+            auto pk = [](int j) { return j >= R ? j - R : B - R + j; };
+            // ---- vertical segment sums -> S for row ys = ybase + j - r
             float s1 = 0.f, s2 = 0.f, cnt = 0.f;
             unsigned cm = 0;
 #pragma unroll
             for (int sgm = 0; sgm < NP; ++sgm) {
 #pragma unroll
-                for (int o = 0; o < L; ++o) raw[o] = col_s ? hE[(sgm * L + o) * SX + t] : 0.f;
-#pragma unroll
                 for (int o = 0; o < L; ++o) {
                     const int j = sgm * L + o;
-                    pre = (o == 0) ? raw[0] : pre + raw[o];
+                    const float h = hE[j * SX + t];
+                    pre = (o == 0) ? h : pre + h;
                     const float Ssum = (o + 1 < L) ? suf[o + 1] + pre : pre;
                     const float2 sy = rowS[j];
                     const float S = Ssum * (sy.y * inv_nx);
                     const bool valid = col_s && sy.x > 0.f && S > 0.f;
                     const float rv = (j >= R) ? cur[(j - R) * SD + t + R] : rvp[j < R ? j : 0];
-                    float snr = 0.f;
-                    if (valid) {
-                        snr = rv * rsqrtf(S);
-                        s1 += snr;
-                        s2 = fmaf(snr, snr, s2);
-                        cnt += 1.f;
-                    }
-                    if (valid && snr > a.kappa) cm |= 1u << j;
-                    hE[j * SX + t] = snr;
+                    // branch-free: an invalid pixel adds exactly +0 to the sums
+                    const float snr = valid ? rv * rsqrtf(S) : 0.f;
+                    s1 += snr;
+                    s2 = fmaf(snr, snr, s2);
+                    cnt += valid ? 1.f : 0.f;
+                    cm |= (valid && snr > a.kappa) ? 1u << j : 0u;
+                    park[pk(j) * SD] = snr;
                 }
-                // suffix sums of the finished segment for the next one
+                // suffix sums of the finished segment for the next one (hE is intact)
                 float acc = 0.f;
 #pragma unroll
-                for (int i = L - 1; i >= 1; --i) { acc += raw[i]; suf[i] = acc; }
+                for (int i = L - 1; i >= 1; --i) { acc += hE[(sgm * L + i) * SX + t]; suf[i] = acc; }
             }
             d1 += s1;
             d2 += s2;
@@ -302,10 +311,9 @@ __global__ void __launch_bounds__(ResGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
                 const int j = __ffs(any) - 1;
                 any &= any - 1;
                 const bool cand = (cm >> j) & 1u;
-                emit_res_candidates(ra, row, ybase + j - R, xs, cand ? hE[j * SX + t] : 0.f, cand, m0, nm);
+                emit_res_candidates(ra, row, ybase + j - R, xs, cand ? park[pk(j) * SD] : 0.f, cand, m0, nm);
             }
         }
-        __syncthreads();
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
 #pragma unroll
