@@ -37,6 +37,11 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool val
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
                  "r"(valid ? 4 : 0));
 }
+// 16-byte copy; both addresses 16-byte aligned
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 
 // (n_y, 1/n_y) of an image row's clipped vertical window; n_y = 0 outside the image.

@@ -162,6 +162,70 @@ __device__ __noinline__ void emit_res_candidates(const ResArgs& ra, int row, int
 }
 
 // ---------------------------------------------------------------------------
+// Geometry of k_filter_res: R rows in shared memory start on 16-byte
+// boundaries (column 0 is image column x0 - A, A = r rounded up to a multiple
+// of 4), so they are copied 16 bytes at a time and read as float4.  The pitch
+// SD = 4 (mod 32) words makes the float4 reads of 32 lanes on 32 rows
+// conflict-free (8 lanes per wavefront, each on its own 16-byte bank group).
+template <int R>
+struct FiltGeom {
+    static constexpr int TX = 128;
+    static constexpr int L = 2 * R + 1;
+    static constexpr int NP = 32 / L;
+    static constexpr int B = NP * L;                         // rows per block
+    static constexpr int A = (R + 3) & ~3;                   // left margin
+    static constexpr int WL = (TX + A + R + 3) & ~3;         // loaded columns
+    static constexpr int NC = WL / 4;                        // 16-byte chunks per row
+    static constexpr int SD = ((WL + 27) & ~31) + 4;         // pitch, = 4 (mod 32)
+    static constexpr int SX = TX | 1;
+    static constexpr int RR = (2 * R + 1) & ~3;              // run length (multiple of 4, <= 2r+1)
+    static constexpr int NR = (TX + RR - 1) / RR;
+    static constexpr int LAST = TX - (NR - 1) * RR;
+    static constexpr int NT = 160;
+    static_assert(SD >= WL && SD % 32 == 4 && NC >= 32 && NC <= 64, "copy by one warp, two chunks a lane");
+    static_assert(B <= 32 && LAST > 0 && LAST <= RR, "lane = row; ragged last run");
+};
+
+// Horizontal window sums of R^2 for the outputs c0 .. c0 + LEN - 1 (relative to
+// x0) of one shared-memory row: the inputs v[i] = R(x0 + c0 - r + i), i in
+// [0, 2r + LEN), lie at row columns c0 + (A - r) + i.  Two stacks around the
+// pivot i = 2r (SUF of v[o .. 2r-1] + PRE of v[2r .. 2r+o]), squares by fma.
+template <int R, int A, int LEN>
+__device__ __forceinline__ void hsum_sq_run(const float* __restrict__ in, int c0, float* __restrict__ out) {
+    constexpr int OFF = A - R;
+    constexpr int NS = LEN < 2 * R ? LEN : 2 * R;
+    float suf[NS];
+    float acc = 0.f;
+#pragma unroll
+    for (int q = (OFF + 2 * R - 1) / 4; q >= 0; --q) {
+        const float4 c = *reinterpret_cast<const float4*>(in + c0 + 4 * q);
+        const float e[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int k = 3; k >= 0; --k) {
+            const int i = 4 * q + k - OFF;
+            if (i >= 0 && i < 2 * R) {
+                acc = fmaf(e[k], e[k], acc);
+                if (i < NS) suf[i < NS ? i : 0] = acc;
+            }
+        }
+    }
+    float pre = 0.f;
+#pragma unroll
+    for (int q = (OFF + 2 * R) / 4; q <= (OFF + 2 * R + LEN - 1) / 4; ++q) {
+        const float4 c = *reinterpret_cast<const float4*>(in + c0 + 4 * q);
+        const float e[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = 4 * q + k - OFF;
+            if (i >= 2 * R && i < 2 * R + LEN) {
+                pre = fmaf(e[k], e[k], pre);
+                const int o = i - 2 * R;
+                out[c0 + o] = (o < NS) ? suf[o < NS ? o : 0] + pre : pre;
+            }
+        }
+    }
+}
+
 // k_filter_res: per distinct row (blockIdx.y) and 128-column strip, streaming
 // down in blocks of B rows of R = D - C held in a double buffer (block k being
 // used, block k+1 being copied in):
@@ -176,16 +240,15 @@ __device__ __noinline__ void emit_res_candidates(const ResArgs& ra, int row, int
 //      warp 4 meanwhile issues the cp.async copies of block k+1.
 //   One barrier per block publishes the copies and separates the vertical pass
 //   of block k-1 from the horizontal pass of block k; a second one separates
-//   the horizontal and vertical passes of block k.
+//   the horizontal and vertical passes of block k.  A pixel outside the image
+//   has a zero column or row factor, so S = 0 there and it is not valid.
 template <int R>
-__global__ void __launch_bounds__(ResGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
-    using G = ResGeom<R>;
-    constexpr int TX = G::TX, B = G::B, L = G::L, SD = G::SD, SX = G::SX, WD = G::WD, NT = G::NT;
-    constexpr int NP = G::NP, RR = G::RR, NR = G::NR;
-    constexpr int LAST = TX - (NR - 1) * RR;         // columns of the last run
-    static_assert(B <= 32 && LAST > 0 && LAST <= RR, "lane = row; ragged last run");
-    extern __shared__ float sm[];
-    float* Rb = sm;                     // [2][B][SD] R rows; col = x - (x0 - r)
+__global__ void __launch_bounds__(FiltGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
+    using G = FiltGeom<R>;
+    constexpr int TX = G::TX, B = G::B, L = G::L, SD = G::SD, SX = G::SX, NT = G::NT;
+    constexpr int NP = G::NP, RR = G::RR, NR = G::NR, A = G::A, WL = G::WL, NC = G::NC;
+    extern __shared__ __align__(16) float sm[];
+    float* Rb = sm;                     // [2][B][SD] R rows; col = x - (x0 - A)
     float* hE = Rb + 2 * B * SD;        // [B][SX]
     __shared__ float2 rowS[B];
     const FilterArgs& a = ra.a;
@@ -200,7 +263,8 @@ __global__ void __launch_bounds__(ResGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
     const bool col_s = t < TX && xs < W;
     const int nx = col_s ? min(xs + R, W - 1) - max(xs - R, 0) + 1 : 0;
     const float inv_nx = col_s ? 1.0f / (float)nx : 0.f;
-    const bool interior = x0 - R >= 0 && x0 - R + WD <= W;
+    // 16-byte copies need whole chunks inside the image and 16-byte aligned rows
+    const bool vec_cols = x0 - A >= 0 && x0 - A + WL <= W && (W & 3) == 0;
     float suf[L];
 #pragma unroll
     for (int i = 0; i < L; ++i) suf[i] = 0.f;
@@ -212,15 +276,24 @@ __global__ void __launch_bounds__(ResGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
     auto load = [&](int kk, int t0, int nthr) {
         float* dst = Rb + (kk & 1) * B * SD;
         const int yb = kk * B;
-        if (interior && yb + B <= H) {
-            for (int c = t - t0; c < WD; c += nthr) {
-                const float* src = Rimg + (int64_t)yb * W + (x0 - R + c);
+        const int u = t - t0;
+        if (vec_cols && yb + B <= H) {
+            const float* src = Rimg + (int64_t)yb * W + (x0 - A);
+            if (nthr == 32) {
 #pragma unroll
-                for (int j = 0; j < B; ++j) cp_async4(dst + j * SD + c, src + (int64_t)j * W, true);
+                for (int j = 0; j < B; ++j) {
+                    cp_async16(dst + j * SD + 4 * u, src + (int64_t)j * W + 4 * u);
+                    if (u + 32 < NC) cp_async16(dst + j * SD + 4 * (u + 32), src + (int64_t)j * W + 4 * (u + 32));
+                }
+            } else {
+                for (int i = u; i < B * NC; i += nthr) {
+                    const int j = i / NC, ch = i - j * NC;
+                    cp_async16(dst + j * SD + 4 * ch, src + (int64_t)j * W + 4 * ch);
+                }
             }
         } else {
-            for (int c = t - t0; c < WD; c += nthr) {
-                const int x = x0 - R + c;
+            for (int c = u; c < WL; c += nthr) {
+                const int x = x0 - A + c;
                 const bool colok = x >= 0 && x < W;
                 const float* src = Rimg + (int64_t)yb * W + x;
 #pragma unroll 4
@@ -243,15 +316,11 @@ __global__ void __launch_bounds__(ResGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
         asm volatile("cp.async.wait_group 0;\n" ::);
         __syncthreads();
         if (t < B) rowS[t] = row_count<R>(ybase + t - R, H);
-        // ---- horizontal window sums of R^2 over buffer cols c .. c + 2r (output col x0 + c)
+        // ---- horizontal window sums of R^2 (output col x0 + c), warp = run, lane = row
         for (int ru = warp; ru < NR; ru += NT / 32) {
             if (lane < B) {
-                const float* in = cur + lane * SD;
-                float* out = hE + lane * SX;
-                auto ld = [&](int c) { float r = in[c]; return r * r; };
-                auto st = [&](int c, float v) { out[c] = v; };
-                if (ru < NR - 1) two_stack_run<R, RR>(ru * RR, RR, ld, st);
-                else two_stack_run<R, LAST>((NR - 1) * RR, LAST, ld, st);
+                if (ru < NR - 1) hsum_sq_run<R, A, RR>(cur + lane * SD, ru * RR, hE + lane * SX);
+                else hsum_sq_run<R, A, G::LAST>(cur + lane * SD, (NR - 1) * RR, hE + lane * SX);
             }
         }
         __syncthreads();
@@ -272,7 +341,7 @@ __global__ void __launch_bounds__(ResGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
             // of its own centre value (j >= r, read just before) or one of the last
             // r rows, which this pass does not read (the next pass reads them from
             // global memory and the buffer is refilled only after the next barrier)
-            float* park = Rb + (k & 1) * B * SD + t + R;
+            float* park = Rb + (k & 1) * B * SD + t + A;
             auto pk = [](int j) { return j >= R ? j - R : B - R + j; };
             // ---- vertical segment sums -> S for row ys = ybase + j - r
             float s1 = 0.f, s2 = 0.f, cnt = 0.f;
@@ -285,10 +354,9 @@ __global__ void __launch_bounds__(ResGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
                     const float h = hE[j * SX + t];
                     pre = (o == 0) ? h : pre + h;
                     const float Ssum = (o + 1 < L) ? suf[o + 1] + pre : pre;
-                    const float2 sy = rowS[j];
-                    const float S = Ssum * (sy.y * inv_nx);
-                    const bool valid = col_s && sy.x > 0.f && S > 0.f;
-                    const float rv = (j >= R) ? cur[(j - R) * SD + t + R] : rvp[j < R ? j : 0];
+                    const float S = Ssum * (rowS[j].y * inv_nx);
+                    const bool valid = S > 0.f;
+                    const float rv = (j >= R) ? cur[(j - R) * SD + t + A] : rvp[j < R ? j : 0];
                     // branch-free: an invalid pixel adds exactly +0 to the sums
                     const float snr = valid ? rv * rsqrtf(S) : 0.f;
                     s1 += snr;
@@ -340,7 +408,7 @@ constexpr size_t residual_smem_bytes() {
 
 template <int R>
 constexpr size_t res_filter_smem_bytes() {
-    return ((size_t)2 * ResGeom<R>::B * ResGeom<R>::SD + (size_t)ResGeom<R>::B * ResGeom<R>::SX) * sizeof(float);
+    return ((size_t)2 * FiltGeom<R>::B * FiltGeom<R>::SD + (size_t)FiltGeom<R>::B * FiltGeom<R>::SX) * sizeof(float);
 }
 
 }  // namespace lpf

@@ -297,9 +297,9 @@ void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows) {
     ra.Dd = s->Dd;
     dim3 grid((unsigned)s->n_strips, (unsigned)n_rows);
     if (s->prm.box_r == 7)
-        lpf::k_filter_res<7><<<grid, lpf::ResGeom<7>::NT, lpf::res_filter_smem_bytes<7>(), s->st>>>(ra);
+        lpf::k_filter_res<7><<<grid, lpf::FiltGeom<7>::NT, lpf::res_filter_smem_bytes<7>(), s->st>>>(ra);
     else
-        lpf::k_filter_res<15><<<grid, lpf::ResGeom<15>::NT, lpf::res_filter_smem_bytes<15>(), s->st>>>(ra);
+        lpf::k_filter_res<15><<<grid, lpf::FiltGeom<15>::NT, lpf::res_filter_smem_bytes<15>(), s->st>>>(ra);
 }
 
 template <typename TS>
