@@ -136,9 +136,12 @@ int lpf_stream_footprint(int H, int W, int F, const double* freqs_mhz, int n_dm,
  */
 int lpf_push_frame(lpf_stream* s, const float* frame_dev, int64_t T);
 
-/* Same as lpf_push_frame with a HOST frame (pinned or pageable), copied to the
- * device inside the call's stream order; the host buffer may be reused when the
- * call returns if it is pageable, after the next poll if it is pinned. */
+/* Same as lpf_push_frame with a HOST frame (pinned or pageable).  The frame is
+ * copied into one of two device staging buffers on a separate upload stream,
+ * so the upload of frame T overlaps the search of frame T-1; the search of T
+ * starts when its upload is done.  The host buffer may be reused when the call
+ * returns if it is pageable, once lpf_poll_candidates has returned T (or after
+ * lpf_stream_sync) if it is pinned. */
 int lpf_push_frame_host(lpf_stream* s, const float* frame_host, int64_t T);
 
 /*

@@ -70,7 +70,11 @@ struct lpf_stream {
     // device memory
     void* ring = nullptr;
     float* D = nullptr;
-    float* stage = nullptr;          // host-push staging frame
+    float* stage = nullptr;          // host-push staging frames [2][F][HW]
+    cudaStream_t h2d_st = nullptr;   // uploads of host frames
+    cudaEvent_t stage_ready[2] = {nullptr, nullptr};   // upload into stage i done
+    cudaEvent_t stage_free[2] = {nullptr, nullptr};    // push that read stage i done
+    int stage_next = 0;
     int16_t* d_lag = nullptr;
     uint32_t* d_chg = nullptr;      // per distinct row: subbands whose lag differs from the previous row
     int* d_member_start = nullptr;
@@ -163,6 +167,14 @@ void free_all(lpf_stream* s) {
             if (e) cudaEventDestroy(e);
     if (s->h_count) cudaFreeHost(s->h_count);
     if (s->h_stats) cudaFreeHost(s->h_stats);
+    for (int i = 0; i < 2; ++i) {
+        if (s->stage_ready[i]) cudaEventDestroy(s->stage_ready[i]);
+        if (s->stage_free[i]) cudaEventDestroy(s->stage_free[i]);
+    }
+    if (s->h2d_st) {
+        cudaStreamSynchronize(s->h2d_st);
+        cudaStreamDestroy(s->h2d_st);
+    }
     if (s->copy_st) cudaStreamDestroy(s->copy_st);
     if (s->own_stream && s->st) cudaStreamDestroy(s->st);
 }
@@ -595,7 +607,7 @@ size_t footprint_bytes(const lpf_stream* s) {
     auto b = [](size_t n) { return std::max<size_t>(n, 16); };
     const size_t nd = (size_t)s->n_distinct, cap = (size_t)s->prm.cand_cap;
     size_t t = (size_t)s->depth * s->F * s->P * s->elem * (s->stream_filter ? 2 : 1);
-    t += b(nd * s->P * 4) * (s->stream_filter ? 2 : 1) + b((size_t)s->F * s->HW * 4) + b(nd * s->F * 2) + b(nd * 4);
+    t += b(nd * s->P * 4) * (s->stream_filter ? 2 : 1) + b(2 * (size_t)s->F * s->HW * 4) + b(nd * s->F * 2) + b(nd * 4);
     t += b(s->member_start.size() * 4) + b(s->member_ord.size() * 4) + 2 * b((size_t)s->n_dm * 4);
     t += 2 * (b(cap * 8) + b(cap * 4)) + b(16) + b((size_t)256 * kSortBlocks * 4);
     t += b(nd * n_filter_blocks(s) * 3 * 8);
@@ -640,6 +652,11 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
         s->own_stream = true;
     }
     if (cudaStreamCreateWithFlags(&s->copy_st, cudaStreamNonBlocking) != cudaSuccess) rc = LPF_E_CUDA;
+    if (rc == LPF_OK && cudaStreamCreateWithFlags(&s->h2d_st, cudaStreamNonBlocking) != cudaSuccess) rc = LPF_E_CUDA;
+    for (int i = 0; i < 2 && rc == LPF_OK; ++i)
+        if (cudaEventCreateWithFlags(&s->stage_ready[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s->stage_free[i], cudaEventDisableTiming) != cudaSuccess)
+            rc = LPF_E_CUDA;
     if (rc == LPF_OK && cudaFuncSetAttribute(lpf::k_filter<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)filter_smem_bytes(8, 8)) != cudaSuccess) rc = LPF_E_CUDA;
     if (rc == LPF_OK && cudaFuncSetAttribute(lpf::k_filter<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -660,7 +677,7 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
     }
     if (rc == LPF_OK) rc = dev_alloc(s, &s->D, (size_t)s->n_distinct * s->P);
     if (rc == LPF_OK && s->stream_filter) rc = dev_alloc(s, &s->Dd, (size_t)s->n_distinct * s->P);
-    if (rc == LPF_OK) rc = dev_alloc(s, &s->stage, (size_t)F * s->HW);
+    if (rc == LPF_OK) rc = dev_alloc(s, &s->stage, 2 * (size_t)F * s->HW);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_lag, (size_t)s->n_distinct * F);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_chg, (size_t)s->n_distinct);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_member_start, s->member_start.size());
@@ -734,8 +751,20 @@ int lpf_push_frame_host(lpf_stream* s, const float* frame_host, int64_t T) {
     if (rc != LPF_OK) return rc;
     if (!frame_host) return LPF_E_ARG;
     if (cudaSetDevice(s->dev) != cudaSuccess) return LPF_E_CUDA;
-    LPF_TRY(cudaMemcpyAsync(s->stage, frame_host, sizeof(float) * s->F * s->HW, cudaMemcpyHostToDevice, s->st));
-    return enqueue_push(s, s->stage, T);
+    // Double-buffered upload on its own stream: the copy of this frame overlaps
+    // the search of the previous one; the stream's work waits for the copy, and
+    // the next upload into this buffer waits for this push to finish reading it.
+    const int i = s->stage_next;
+    float* stage = s->stage + (size_t)i * s->F * s->HW;
+    LPF_TRY(cudaStreamWaitEvent(s->h2d_st, s->stage_free[i], 0));
+    LPF_TRY(cudaMemcpyAsync(stage, frame_host, sizeof(float) * s->F * s->HW, cudaMemcpyHostToDevice, s->h2d_st));
+    LPF_TRY(cudaEventRecord(s->stage_ready[i], s->h2d_st));
+    LPF_TRY(cudaStreamWaitEvent(s->st, s->stage_ready[i], 0));
+    rc = enqueue_push(s, stage, T);
+    if (rc != LPF_OK) return rc;
+    LPF_TRY(cudaEventRecord(s->stage_free[i], s->st));
+    s->stage_next = i ^ 1;
+    return LPF_OK;
 }
 
 int lpf_poll_candidates(lpf_stream* s, lpf_candidate* out_host, int cap, int* n_out, int64_t* T_out,
