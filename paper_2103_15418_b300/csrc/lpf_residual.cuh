@@ -16,6 +16,15 @@
 
 namespace lpf {
 
+// 1/sqrt(x) for a normal FP32 x (x >= 2^-126): the approximate reciprocal
+// square root instruction, whose relative error is a few units in the last
+// place; no subnormal handling is needed on that range.
+__device__ __forceinline__ float rsqrt_normal(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 template <int R>
 struct ResGeom {
     static constexpr int TX = 128;
@@ -118,7 +127,13 @@ __global__ void __launch_bounds__(ResGeom<R>::NT) k_residual(const TS* __restric
 struct ResArgs {
     FilterArgs a;            // R = D - C images in a.D, emission, stats
     const float* Dd;         // [n_rows][P] D images (shift-sum of the raw ring), for the 3x3 maximum
+    uint64_t* xkeys;         // [a.cap] threshold crossings (row << 32 | y << 16 | x) ...
+    float* xvals;            // ... and their S/N
+    unsigned long long* xcounter;   // crossings reserved (may exceed a.cap)
 };
+
+// a crossing slot reserved by a warp that resolved its crossings itself
+constexpr uint64_t kNoCrossing = ~0ull;
 
 // Candidates of one image row of a warp (lanes with cand set): the 3x3 local
 // maximum of D clipped to the image (ties count), from the dedispersed image of
@@ -355,10 +370,11 @@ __global__ void __launch_bounds__(FiltGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
                     pre = (o == 0) ? h : pre + h;
                     const float Ssum = (o + 1 < L) ? suf[o + 1] + pre : pre;
                     const float S = Ssum * (rowS[j].y * inv_nx);
-                    const bool valid = S > 0.f;
+                    // a spread below the smallest normal FP32 number counts as none
+                    const bool valid = S >= 1.17549435e-38f;
                     const float rv = (j >= R) ? cur[(j - R) * SD + t + A] : rvp[j < R ? j : 0];
                     // branch-free: an invalid pixel adds exactly +0 to the sums
-                    const float snr = valid ? rv * rsqrtf(S) : 0.f;
+                    const float snr = valid ? rv * rsqrt_normal(S) : 0.f;
                     s1 += snr;
                     s2 = fmaf(snr, snr, s2);
                     cnt += valid ? 1.f : 0.f;
@@ -373,13 +389,41 @@ __global__ void __launch_bounds__(FiltGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
             d1 += s1;
             d2 += s2;
             dc += cnt;
-            // ---- candidates of this block (rare): rows with a set bit anywhere in the warp
-            unsigned any = __reduce_or_sync(0xffffffffu, cm);
-            while (any) {
-                const int j = __ffs(any) - 1;
-                any &= any - 1;
-                const bool cand = (cm >> j) & 1u;
-                emit_res_candidates(ra, row, ybase + j - R, xs, cand ? park[pk(j) * SD] : 0.f, cand, m0, nm);
+            // ---- threshold crossings of this block: one reservation per warp in
+            // the crossing list (the 3x3 maximum of D is taken by k_lmax_res); a
+            // warp whose reservation does not fit voids it and resolves its
+            // crossings here, so every crossing is resolved exactly once
+            if (__reduce_or_sync(0xffffffffu, cm)) {
+                const unsigned mine = __popc(cm);
+                unsigned incl = mine;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+                unsigned long long base = 0;
+                if (lane == 31) base = atomicAdd(ra.xcounter, (unsigned long long)total);
+                base = __shfl_sync(0xffffffffu, base, 31);
+                if (base + total <= (unsigned long long)a.cap) {
+                    unsigned long long idx = base + incl - mine;
+                    for (unsigned b = cm; b; b &= b - 1) {
+                        const int j = __ffs(b) - 1;
+                        ra.xkeys[idx] = ((uint64_t)row << 32) | ((uint64_t)(ybase + j - R) << 16) | (uint64_t)xs;
+                        ra.xvals[idx] = park[pk(j) * SD];
+                        ++idx;
+                    }
+                } else {
+                    for (unsigned long long i = base + lane; i < base + total && i < (unsigned long long)a.cap; i += 32)
+                        ra.xkeys[i] = kNoCrossing;
+                    unsigned any = __reduce_or_sync(0xffffffffu, cm);
+                    while (any) {
+                        const int j = __ffs(any) - 1;
+                        any &= any - 1;
+                        const bool cand = (cm >> j) & 1u;
+                        emit_res_candidates(ra, row, ybase + j - R, xs, cand ? park[pk(j) * SD] : 0.f, cand, m0, nm);
+                    }
+                }
             }
         }
     }
@@ -398,6 +442,69 @@ __global__ void __launch_bounds__(FiltGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
         for (int w = 0; w < NT / 32; ++w) { q1 += red[w][0]; q2 += red[w][1]; qc += red[w][2]; }
         double* p = a.partials + ((int64_t)row * gridDim.x + strip) * 3;
         p[0] = q1; p[1] = q2; p[2] = qc;
+    }
+}
+
+// k_lmax_res: the 3x3 local maximum of D (clipped to the image, ties count) at
+// every crossing of the list, one thread per crossing, and one candidate record
+// per DM trial of a maximum's delay row (warp-aggregated reservations).
+__global__ void __launch_bounds__(256) k_lmax_res(ResArgs ra) {
+    const FilterArgs& a = ra.a;
+    const unsigned long long nres = *ra.xcounter;
+    const unsigned n = (unsigned)(nres < (unsigned long long)a.cap ? nres : (unsigned long long)a.cap);
+    const int lane = threadIdx.x & 31;
+    const unsigned nwarps = gridDim.x * (blockDim.x >> 5);
+    const unsigned gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int H = a.H, W = a.W;
+    for (unsigned i0 = gw * 32u; i0 < n; i0 += nwarps * 32u) {
+        const unsigned i = i0 + lane;
+        bool cand = false;
+        int row = 0, ys = 0, xs = 0;
+        float snr = 0.f;
+        if (i < n) {
+            const uint64_t key = ra.xkeys[i];
+            if (key != kNoCrossing) {
+                row = (int)(key >> 32);
+                ys = (int)((key >> 16) & 0xffffu);
+                xs = (int)(key & 0xffffu);
+                snr = ra.xvals[i];
+                const float* p = ra.Dd + (int64_t)row * a.P + (int64_t)ys * W + xs;
+                float nb[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    const int yy = ys + k / 3 - 1, xx = xs + k % 3 - 1;
+                    nb[k] = (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                                ? __ldg(p + (int64_t)(k / 3 - 1) * W + (k % 3 - 1)) : -INFINITY;
+                }
+                cand = true;
+#pragma unroll
+                for (int k = 0; k < 9; ++k)
+                    if (k != 4 && nb[k] > nb[4]) cand = false;
+            }
+        }
+        const int m0 = cand ? a.member_start[row] : 0;
+        const unsigned nm = cand ? (unsigned)(a.member_start[row + 1] - m0) : 0u;
+        unsigned incl = nm;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total == 0) continue;
+        unsigned base = 0;
+        if (lane == 31) base = atomicAdd(a.counter, total);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        if (cand) {
+            const uint64_t pix = ((uint64_t)ys << a.bx) | (uint64_t)xs;
+            for (unsigned m = 0; m < nm; ++m) {
+                const unsigned idx = base + incl - nm + m;
+                if (idx < (unsigned)a.cap) {
+                    a.keys[idx] = ((uint64_t)a.member_ord[m0 + m] << (a.bx + a.by)) | pix;
+                    a.vals[idx] = snr;
+                }
+            }
+        }
     }
 }
 

@@ -307,11 +307,16 @@ void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows) {
     lpf::ResArgs ra;
     ra.a = a;
     ra.Dd = s->Dd;
+    // the crossing list lives in the sort's second key/value buffers, unused until the sort
+    ra.xkeys = s->keys[1];
+    ra.xvals = s->vals[1];
+    ra.xcounter = reinterpret_cast<unsigned long long*>(s->d_counter + 2);
     dim3 grid((unsigned)s->n_strips, (unsigned)n_rows);
     if (s->prm.box_r == 7)
         lpf::k_filter_res<7><<<grid, lpf::FiltGeom<7>::NT, lpf::res_filter_smem_bytes<7>(), s->st>>>(ra);
     else
         lpf::k_filter_res<15><<<grid, lpf::FiltGeom<15>::NT, lpf::res_filter_smem_bytes<15>(), s->st>>>(ra);
+    lpf::k_lmax_res<<<148 * 8, 256, 0, s->st>>>(ra);
 }
 
 template <typename TS>
@@ -434,7 +439,7 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
             default: launch_residual<__nv_bfloat16>(s, ring_slot); break;
         }
     }
-    lpf::k_zero_u32<<<1, 32, 0, s->st>>>(s->d_counter, 1);
+    lpf::k_zero_u32<<<1, 32, 0, s->st>>>(s->d_counter, 4);   // candidates, crossings (u64 at word 2)
     prof_mark(s, sl, ST_DEDISP);
     if (n_rows > 0) {
         switch (s->prm.dtype) {
