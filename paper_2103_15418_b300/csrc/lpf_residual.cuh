@@ -126,7 +126,9 @@ __global__ void __launch_bounds__(ResGeom<R>::NT) k_residual(const TS* __restric
 // ---------------------------------------------------------------------------
 struct ResArgs {
     FilterArgs a;            // R = D - C images in a.D, emission, stats
-    const float* Dd;         // [n_rows][P] D images (shift-sum of the raw ring), for the 3x3 maximum
+    const void* ring;        // raw ring [depth][F][P] (storage type), for D at 3x3 windows
+    const int16_t* lag;      // [n_rows][F] frames back from the newest frame (slot Tmod)
+    int F, depth, Tmod;
     uint64_t* xkeys;         // [a.cap] threshold crossings (row << 32 | y << 16 | x) ...
     float* xvals;            // ... and their S/N
     unsigned long long* xcounter;   // crossings reserved (may exceed a.cap)
@@ -135,24 +137,50 @@ struct ResArgs {
 // a crossing slot reserved by a warp that resolved its crossings itself
 constexpr uint64_t kNoCrossing = ~0ull;
 
+// D = sum_f X_f(t_f) of a delay row on the 3x3 window around (ys, xs), summed
+// from the raw ring in the order f = 0 .. F-1 in FP32 (the arithmetic of the
+// shift-sum, so the same values); -inf outside the image.
+template <typename TS>
+__device__ __forceinline__ void d_window3(const ResArgs& ra, int row, int ys, int xs, float nb[9]) {
+    const FilterArgs& a = ra.a;
+    const int H = a.H, W = a.W;
+    const TS* ring = static_cast<const TS*>(ra.ring);
+    const int16_t* lr = ra.lag + (int64_t)row * ra.F;
+    int64_t off[9];
+    bool in[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int yy = ys + k / 3 - 1, xx = xs + k % 3 - 1;
+        in[k] = yy >= 0 && yy < H && xx >= 0 && xx < W;
+        off[k] = in[k] ? (int64_t)yy * W + xx : 0;
+    }
+    for (int f = 0; f < ra.F; ++f) {
+        int slot = ra.Tmod - (int)__ldg(lr + f);
+        if (slot < 0) slot += ra.depth;
+        const TS* plane = ring + ((int64_t)slot * ra.F + f) * a.P;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float v = in[k] ? ld1(plane + off[k]) : 0.f;
+            nb[k] = (f == 0) ? v : nb[k] + v;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+        if (!in[k]) nb[k] = -INFINITY;
+}
+
 // Candidates of one image row of a warp (lanes with cand set): the 3x3 local
-// maximum of D clipped to the image (ties count), from the dedispersed image of
-// the raw ring; then one warp-aggregated reservation and one record per DM
-// trial of the delay row.  Every lane of the warp calls it.
+// maximum of D clipped to the image (ties count); then one warp-aggregated
+// reservation and one record per DM trial of the delay row.  Every lane of the
+// warp calls it.
+template <typename TS>
 __device__ __noinline__ void emit_res_candidates(const ResArgs& ra, int row, int ys, int xs, float snr,
                                                  bool cand, int m0, int nm) {
     const FilterArgs& a = ra.a;
-    const int H = a.H, W = a.W;
     const int lane = threadIdx.x & 31;
     if (cand) {
-        const float* p = ra.Dd + (int64_t)row * a.P + (int64_t)ys * W + xs;
         float nb[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            int yy = ys + k / 3 - 1, xx = xs + k % 3 - 1;
-            nb[k] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? __ldg(p + (int64_t)(k / 3 - 1) * W + (k % 3 - 1))
-                                                             : -INFINITY;
-        }
+        d_window3<TS>(ra, row, ys, xs, nb);
 #pragma unroll
         for (int k = 0; k < 9; ++k)
             if (k != 4 && nb[k] > nb[4]) cand = false;
@@ -257,7 +285,7 @@ __device__ __forceinline__ void hsum_sq_run(const float* __restrict__ in, int c0
 //   of block k-1 from the horizontal pass of block k; a second one separates
 //   the horizontal and vertical passes of block k.  A pixel outside the image
 //   has a zero column or row factor, so S = 0 there and it is not valid.
-template <int R>
+template <int R, typename TS>
 __global__ void __launch_bounds__(FiltGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
     using G = FiltGeom<R>;
     constexpr int TX = G::TX, B = G::B, L = G::L, SD = G::SD, SX = G::SX, NT = G::NT;
@@ -421,7 +449,8 @@ __global__ void __launch_bounds__(FiltGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
                         const int j = __ffs(any) - 1;
                         any &= any - 1;
                         const bool cand = (cm >> j) & 1u;
-                        emit_res_candidates(ra, row, ybase + j - R, xs, cand ? park[pk(j) * SD] : 0.f, cand, m0, nm);
+                        emit_res_candidates<TS>(ra, row, ybase + j - R, xs, cand ? park[pk(j) * SD] : 0.f, cand,
+                                                m0, nm);
                     }
                 }
             }
@@ -446,8 +475,10 @@ __global__ void __launch_bounds__(FiltGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
 }
 
 // k_lmax_res: the 3x3 local maximum of D (clipped to the image, ties count) at
-// every crossing of the list, one thread per crossing, and one candidate record
-// per DM trial of a maximum's delay row (warp-aggregated reservations).
+// every crossing of the list, one thread per crossing, D summed from the raw
+// ring on the window; one candidate record per DM trial of a maximum's delay
+// row (warp-aggregated reservations).
+template <typename TS>
 __global__ void __launch_bounds__(256) k_lmax_res(ResArgs ra) {
     const FilterArgs& a = ra.a;
     const unsigned long long nres = *ra.xcounter;
@@ -455,7 +486,6 @@ __global__ void __launch_bounds__(256) k_lmax_res(ResArgs ra) {
     const int lane = threadIdx.x & 31;
     const unsigned nwarps = gridDim.x * (blockDim.x >> 5);
     const unsigned gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int H = a.H, W = a.W;
     for (unsigned i0 = gw * 32u; i0 < n; i0 += nwarps * 32u) {
         const unsigned i = i0 + lane;
         bool cand = false;
@@ -468,14 +498,8 @@ __global__ void __launch_bounds__(256) k_lmax_res(ResArgs ra) {
                 ys = (int)((key >> 16) & 0xffffu);
                 xs = (int)(key & 0xffffu);
                 snr = ra.xvals[i];
-                const float* p = ra.Dd + (int64_t)row * a.P + (int64_t)ys * W + xs;
                 float nb[9];
-#pragma unroll
-                for (int k = 0; k < 9; ++k) {
-                    const int yy = ys + k / 3 - 1, xx = xs + k % 3 - 1;
-                    nb[k] = (yy >= 0 && yy < H && xx >= 0 && xx < W)
-                                ? __ldg(p + (int64_t)(k / 3 - 1) * W + (k % 3 - 1)) : -INFINITY;
-                }
+                d_window3<TS>(ra, row, ys, xs, nb);
                 cand = true;
 #pragma unroll
                 for (int k = 0; k < 9; ++k)

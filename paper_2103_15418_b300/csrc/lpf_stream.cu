@@ -114,7 +114,6 @@ struct lpf_stream {
     int filter_rmax = 16;
     bool stream_filter = false;     // residual path: k_residual + k_filter_res (box_r 7 or 15)
     void* resring = nullptr;        // [depth][F][P] per-subband residual X - C(X), storage type
-    float* Dd = nullptr;            // [n_distinct][P] D images of the residual path (local maxima)
     int n_strips = 0;
 
     bool profiling = false;
@@ -152,7 +151,7 @@ void free_all(lpf_stream* s) {
     if (!s) return;
     cudaSetDevice(s->dev);
     if (s->st) cudaStreamSynchronize(s->st);
-    void* ptrs[] = {s->ring, s->resring, s->Dd, s->D, s->stage, s->d_lag, s->d_chg, s->d_member_start, s->d_member_ord,
+    void* ptrs[] = {s->ring, s->resring, s->D, s->stage, s->d_lag, s->d_chg, s->d_member_start, s->d_member_ord,
                     s->d_ord2d, s->d_dmax, s->keys[0], s->keys[1], s->vals[0], s->vals[1],
                     s->d_counter, s->d_hist, s->d_partials, s->d_yx};
     for (void* p : ptrs)
@@ -303,20 +302,25 @@ void launch_residual(lpf_stream* s, int64_t slot) {
         lpf::k_residual<15, TS><<<grid, lpf::ResGeom<15>::NT, lpf::residual_smem_bytes<15>(), s->st>>>(raw, res, s->H, s->W, s->P, seg_rows);
 }
 
-void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows) {
+template <typename TS>
+void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows, int Tmod) {
     lpf::ResArgs ra;
     ra.a = a;
-    ra.Dd = s->Dd;
+    ra.ring = s->ring;
+    ra.lag = s->d_lag;
+    ra.F = s->F;
+    ra.depth = s->depth;
+    ra.Tmod = Tmod;
     // the crossing list lives in the sort's second key/value buffers, unused until the sort
     ra.xkeys = s->keys[1];
     ra.xvals = s->vals[1];
     ra.xcounter = reinterpret_cast<unsigned long long*>(s->d_counter + 2);
     dim3 grid((unsigned)s->n_strips, (unsigned)n_rows);
     if (s->prm.box_r == 7)
-        lpf::k_filter_res<7><<<grid, lpf::FiltGeom<7>::NT, lpf::res_filter_smem_bytes<7>(), s->st>>>(ra);
+        lpf::k_filter_res<7, TS><<<grid, lpf::FiltGeom<7>::NT, lpf::res_filter_smem_bytes<7>(), s->st>>>(ra);
     else
-        lpf::k_filter_res<15><<<grid, lpf::FiltGeom<15>::NT, lpf::res_filter_smem_bytes<15>(), s->st>>>(ra);
-    lpf::k_lmax_res<<<148 * 8, 256, 0, s->st>>>(ra);
+        lpf::k_filter_res<15, TS><<<grid, lpf::FiltGeom<15>::NT, lpf::res_filter_smem_bytes<15>(), s->st>>>(ra);
+    lpf::k_lmax_res<TS><<<148 * 8, 256, 0, s->st>>>(ra);
 }
 
 template <typename TS>
@@ -325,9 +329,9 @@ int set_res_attributes() {
                              (int)lpf::residual_smem_bytes<7>()) != cudaSuccess ||
         cudaFuncSetAttribute(lpf::k_residual<15, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)lpf::residual_smem_bytes<15>()) != cudaSuccess ||
-        cudaFuncSetAttribute(lpf::k_filter_res<7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(lpf::k_filter_res<7, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)lpf::res_filter_smem_bytes<7>()) != cudaSuccess ||
-        cudaFuncSetAttribute(lpf::k_filter_res<15>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(lpf::k_filter_res<15, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)lpf::res_filter_smem_bytes<15>()) != cudaSuccess)
         return LPF_E_CUDA;
     return LPF_OK;
@@ -365,12 +369,12 @@ void launch_dedisperse_ring(lpf_stream* s, const void* ring_v, float* out, int n
     }
 }
 
-// Tiled path: D from the raw ring.  Residual path: D from the raw ring (for the
-// local maxima) and R = D - C from the residual ring.
+// Tiled path: D from the raw ring.  Residual path: R = D - C from the residual
+// ring (D itself is summed from the raw ring only on the 3x3 windows of the
+// threshold crossings).
 template <typename TS>
 void launch_dedisperse(lpf_stream* s, int n_rows, int Tmod) {
     if (s->stream_filter) {
-        launch_dedisperse_ring<TS>(s, s->ring, s->Dd, n_rows, Tmod);
         launch_dedisperse_ring<TS>(s, s->resring, s->D, n_rows, Tmod);
     } else {
         launch_dedisperse_ring<TS>(s, s->ring, s->D, n_rows, Tmod);
@@ -457,7 +461,11 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
         a.keys = s->keys[0]; a.vals = s->vals[0]; a.counter = s->d_counter; a.cap = s->prm.cand_cap;
         a.bx = s->bx; a.by = s->by; a.partials = s->d_partials;
         if (s->stream_filter) {
-            launch_filter_res(s, a, n_rows);
+            switch (s->prm.dtype) {
+                case LPF_FP32: launch_filter_res<float>(s, a, n_rows, Tmod); break;
+                case LPF_FP16: launch_filter_res<__half>(s, a, n_rows, Tmod); break;
+                default: launch_filter_res<__nv_bfloat16>(s, a, n_rows, Tmod); break;
+            }
         } else {
             dim3 grid((unsigned)(s->tiles_x * s->tiles_y), (unsigned)n_rows);
             if (s->filter_rmax == 8)
@@ -612,7 +620,7 @@ size_t footprint_bytes(const lpf_stream* s) {
     auto b = [](size_t n) { return std::max<size_t>(n, 16); };
     const size_t nd = (size_t)s->n_distinct, cap = (size_t)s->prm.cand_cap;
     size_t t = (size_t)s->depth * s->F * s->P * s->elem * (s->stream_filter ? 2 : 1);
-    t += b(nd * s->P * 4) * (s->stream_filter ? 2 : 1) + b(2 * (size_t)s->F * s->HW * 4) + b(nd * s->F * 2) + b(nd * 4);
+    t += b(nd * s->P * 4) + b(2 * (size_t)s->F * s->HW * 4) + b(nd * s->F * 2) + b(nd * 4);
     t += b(s->member_start.size() * 4) + b(s->member_ord.size() * 4) + 2 * b((size_t)s->n_dm * 4);
     t += 2 * (b(cap * 8) + b(cap * 4)) + b(16) + b((size_t)256 * kSortBlocks * 4);
     t += b(nd * n_filter_blocks(s) * 3 * 8);
@@ -681,7 +689,6 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
         if (rc == LPF_OK && cudaMemsetAsync(s->resring, 0, ring_elems * s->elem, s->st) != cudaSuccess) rc = LPF_E_CUDA;
     }
     if (rc == LPF_OK) rc = dev_alloc(s, &s->D, (size_t)s->n_distinct * s->P);
-    if (rc == LPF_OK && s->stream_filter) rc = dev_alloc(s, &s->Dd, (size_t)s->n_distinct * s->P);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->stage, 2 * (size_t)F * s->HW);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_lag, (size_t)s->n_distinct * F);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_chg, (size_t)s->n_distinct);
