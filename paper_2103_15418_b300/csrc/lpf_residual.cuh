@@ -129,9 +129,10 @@ struct ResArgs {
     const void* ring;        // raw ring [depth][F][P] (storage type), for D at 3x3 windows
     const int16_t* lag;      // [n_rows][F] frames back from the newest frame (slot Tmod)
     int F, depth, Tmod;
-    uint64_t* xkeys;         // [a.cap] threshold crossings (row << 32 | y << 16 | x) ...
+    uint64_t* xkeys;         // [xcap] threshold crossings (row << 32 | y << 16 | x) ...
     float* xvals;            // ... and their S/N
-    unsigned long long* xcounter;   // crossings reserved (may exceed a.cap)
+    unsigned long long* xcounter;   // crossings reserved (may exceed xcap)
+    int64_t xcap;            // crossing list capacity
 };
 
 // a crossing slot reserved by a warp that resolved its crossings itself
@@ -169,6 +170,31 @@ __device__ __forceinline__ void d_window3(const ResArgs& ra, int row, int ys, in
         if (!in[k]) nb[k] = -INFINITY;
 }
 
+// The same values one window pixel at a time (few registers: the in-kernel
+// resolution of an overflowing crossing list).
+template <typename TS>
+__device__ __forceinline__ void d_window3_lean(const ResArgs& ra, int row, int ys, int xs, float nb[9]) {
+    const FilterArgs& a = ra.a;
+    const TS* ring = static_cast<const TS*>(ra.ring);
+    const int16_t* lr = ra.lag + (int64_t)row * ra.F;
+#pragma unroll 1
+    for (int k = 0; k < 9; ++k) {
+        const int yy = ys + k / 3 - 1, xx = xs + k % 3 - 1;
+        float v = -INFINITY;
+        if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) {
+            const int64_t off = (int64_t)yy * a.W + xx;
+#pragma unroll 1
+            for (int f = 0; f < ra.F; ++f) {
+                int slot = ra.Tmod - (int)__ldg(lr + f);
+                if (slot < 0) slot += ra.depth;
+                const float x = ld1(ring + ((int64_t)slot * ra.F + f) * a.P + off);
+                v = (f == 0) ? x : v + x;
+            }
+        }
+        nb[k] = v;
+    }
+}
+
 // Candidates of one image row of a warp (lanes with cand set): the 3x3 local
 // maximum of D clipped to the image (ties count); then one warp-aggregated
 // reservation and one record per DM trial of the delay row.  Every lane of the
@@ -180,7 +206,7 @@ __device__ __noinline__ void emit_res_candidates(const ResArgs& ra, int row, int
     const int lane = threadIdx.x & 31;
     if (cand) {
         float nb[9];
-        d_window3<TS>(ra, row, ys, xs, nb);
+        d_window3_lean<TS>(ra, row, ys, xs, nb);
 #pragma unroll
         for (int k = 0; k < 9; ++k)
             if (k != 4 && nb[k] > nb[4]) cand = false;
@@ -433,7 +459,7 @@ __global__ void __launch_bounds__(FiltGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
                 unsigned long long base = 0;
                 if (lane == 31) base = atomicAdd(ra.xcounter, (unsigned long long)total);
                 base = __shfl_sync(0xffffffffu, base, 31);
-                if (base + total <= (unsigned long long)a.cap) {
+                if (base + total <= (unsigned long long)ra.xcap) {
                     unsigned long long idx = base + incl - mine;
                     for (unsigned b = cm; b; b &= b - 1) {
                         const int j = __ffs(b) - 1;
@@ -442,7 +468,7 @@ __global__ void __launch_bounds__(FiltGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
                         ++idx;
                     }
                 } else {
-                    for (unsigned long long i = base + lane; i < base + total && i < (unsigned long long)a.cap; i += 32)
+                    for (unsigned long long i = base + lane; i < base + total && i < (unsigned long long)ra.xcap; i += 32)
                         ra.xkeys[i] = kNoCrossing;
                     unsigned any = __reduce_or_sync(0xffffffffu, cm);
                     while (any) {
@@ -482,12 +508,12 @@ template <typename TS>
 __global__ void __launch_bounds__(256) k_lmax_res(ResArgs ra) {
     const FilterArgs& a = ra.a;
     const unsigned long long nres = *ra.xcounter;
-    const unsigned n = (unsigned)(nres < (unsigned long long)a.cap ? nres : (unsigned long long)a.cap);
+    const unsigned long long n = nres < (unsigned long long)ra.xcap ? nres : (unsigned long long)ra.xcap;
     const int lane = threadIdx.x & 31;
-    const unsigned nwarps = gridDim.x * (blockDim.x >> 5);
-    const unsigned gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    for (unsigned i0 = gw * 32u; i0 < n; i0 += nwarps * 32u) {
-        const unsigned i = i0 + lane;
+    const unsigned long long nwarps = gridDim.x * (blockDim.x >> 5);
+    const unsigned long long gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (unsigned long long i0 = gw * 32u; i0 < n; i0 += nwarps * 32u) {
+        const unsigned long long i = i0 + lane;
         bool cand = false;
         int row = 0, ys = 0, xs = 0;
         float snr = 0.f;

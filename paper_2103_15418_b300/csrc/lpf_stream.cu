@@ -70,6 +70,9 @@ struct lpf_stream {
     // device memory
     void* ring = nullptr;
     float* D = nullptr;
+    uint64_t* xkeys = nullptr;      // threshold crossings of the residual path (row, y, x) ...
+    float* xvals = nullptr;         // ... and their S/N
+    int64_t xcap = 0;               // crossing capacity
     float* stage = nullptr;          // host-push staging frames [2][F][HW]
     cudaStream_t h2d_st = nullptr;   // uploads of host frames
     cudaEvent_t stage_ready[2] = {nullptr, nullptr};   // upload into stage i done
@@ -151,7 +154,7 @@ void free_all(lpf_stream* s) {
     if (!s) return;
     cudaSetDevice(s->dev);
     if (s->st) cudaStreamSynchronize(s->st);
-    void* ptrs[] = {s->ring, s->resring, s->D, s->stage, s->d_lag, s->d_chg, s->d_member_start, s->d_member_ord,
+    void* ptrs[] = {s->ring, s->resring, s->D, s->xkeys, s->xvals, s->stage, s->d_lag, s->d_chg, s->d_member_start, s->d_member_ord,
                     s->d_ord2d, s->d_dmax, s->keys[0], s->keys[1], s->vals[0], s->vals[1],
                     s->d_counter, s->d_hist, s->d_partials, s->d_yx};
     for (void* p : ptrs)
@@ -311,10 +314,10 @@ void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows, int 
     ra.F = s->F;
     ra.depth = s->depth;
     ra.Tmod = Tmod;
-    // the crossing list lives in the sort's second key/value buffers, unused until the sort
-    ra.xkeys = s->keys[1];
-    ra.xvals = s->vals[1];
+    ra.xkeys = s->xkeys;
+    ra.xvals = s->xvals;
     ra.xcounter = reinterpret_cast<unsigned long long*>(s->d_counter + 2);
+    ra.xcap = s->xcap;
     dim3 grid((unsigned)s->n_strips, (unsigned)n_rows);
     if (s->prm.box_r == 7)
         lpf::k_filter_res<7, TS><<<grid, lpf::FiltGeom<7>::NT, lpf::res_filter_smem_bytes<7>(), s->st>>>(ra);
@@ -609,6 +612,11 @@ int plan_stream(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, 
     s->filter_smem = filter_smem_bytes(prm.box_r, s->filter_rmax);
     s->stream_filter = prm.filter_impl == 2 || (prm.filter_impl == 0 && (prm.box_r == 7 || prm.box_r == 15));
     s->n_strips = (W + lpf::kStreamTX - 1) / lpf::kStreamTX;
+    // crossing list of the residual path: room for 1/32 of all pixels of all
+    // delay rows above the threshold (a swamped frame overflows into the slower
+    // in-kernel resolution, with the same results)
+    if (s->stream_filter)
+        s->xcap = std::max<int64_t>(prm.cand_cap, (int64_t)s->n_distinct * s->HW / 32);
 
     *out = s;
     return LPF_OK;
@@ -621,6 +629,7 @@ size_t footprint_bytes(const lpf_stream* s) {
     const size_t nd = (size_t)s->n_distinct, cap = (size_t)s->prm.cand_cap;
     size_t t = (size_t)s->depth * s->F * s->P * s->elem * (s->stream_filter ? 2 : 1);
     t += b(nd * s->P * 4) + b(2 * (size_t)s->F * s->HW * 4) + b(nd * s->F * 2) + b(nd * 4);
+    if (s->xcap > 0) t += b((size_t)s->xcap * 8) + b((size_t)s->xcap * 4);
     t += b(s->member_start.size() * 4) + b(s->member_ord.size() * 4) + 2 * b((size_t)s->n_dm * 4);
     t += 2 * (b(cap * 8) + b(cap * 4)) + b(16) + b((size_t)256 * kSortBlocks * 4);
     t += b(nd * n_filter_blocks(s) * 3 * 8);
@@ -690,6 +699,8 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
     }
     if (rc == LPF_OK) rc = dev_alloc(s, &s->D, (size_t)s->n_distinct * s->P);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->stage, 2 * (size_t)F * s->HW);
+    if (rc == LPF_OK && s->xcap > 0) rc = dev_alloc(s, &s->xkeys, (size_t)s->xcap);
+    if (rc == LPF_OK && s->xcap > 0) rc = dev_alloc(s, &s->xvals, (size_t)s->xcap);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_lag, (size_t)s->n_distinct * F);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_chg, (size_t)s->n_distinct);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_member_start, s->member_start.size());
