@@ -29,8 +29,8 @@ constexpr double kCdmSeconds = 4.148808e3;   // s MHz^2 cm^3 / pc (Sec. 3.2)
 using lpf::kSortBlocks;
 constexpr int kMaxSlots = 16;
 
-enum Stage { ST_INGEST, ST_DEDISP, ST_FILTER, ST_SORT, ST_FORMAT, ST_STATS, ST_N };
-const char* kStageNames[ST_N] = {"ingest", "dedisperse", "filter_detect", "sort", "format", "stats"};
+enum Stage { ST_INGEST, ST_DEDISP, ST_FILTER, ST_LMAX, ST_SORT, ST_FORMAT, ST_STATS, ST_N };
+const char* kStageNames[ST_N] = {"ingest", "dedisperse", "filter_detect", "lmax", "sort", "format", "stats"};
 
 int ceil_log2(int64_t v) {
     int b = 0;
@@ -305,8 +305,7 @@ void launch_residual(lpf_stream* s, int64_t slot) {
         lpf::k_residual<15, TS><<<grid, lpf::ResGeom<15>::NT, lpf::residual_smem_bytes<15>(), s->st>>>(raw, res, s->H, s->W, s->P, seg_rows);
 }
 
-template <typename TS>
-void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows, int Tmod) {
+lpf::ResArgs res_args(lpf_stream* s, const lpf::FilterArgs& a, int Tmod) {
     lpf::ResArgs ra;
     ra.a = a;
     ra.ring = s->ring;
@@ -318,12 +317,22 @@ void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows, int 
     ra.xvals = s->xvals;
     ra.xcounter = reinterpret_cast<unsigned long long*>(s->d_counter + 2);
     ra.xcap = s->xcap;
+    return ra;
+}
+
+template <typename TS>
+void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows, int Tmod) {
+    const lpf::ResArgs ra = res_args(s, a, Tmod);
     dim3 grid((unsigned)s->n_strips, (unsigned)n_rows);
     if (s->prm.box_r == 7)
         lpf::k_filter_res<7, TS><<<grid, lpf::FiltGeom<7>::NT, lpf::res_filter_smem_bytes<7>(), s->st>>>(ra);
     else
         lpf::k_filter_res<15, TS><<<grid, lpf::FiltGeom<15>::NT, lpf::res_filter_smem_bytes<15>(), s->st>>>(ra);
-    lpf::k_lmax_res<TS><<<148 * 8, 256, 0, s->st>>>(ra);
+}
+
+template <typename TS>
+void launch_lmax_res(lpf_stream* s, const lpf::FilterArgs& a, int Tmod) {
+    lpf::k_lmax_res<TS><<<148 * 8, 256, 0, s->st>>>(res_args(s, a, Tmod));
 }
 
 template <typename TS>
@@ -456,8 +465,8 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
         }
     }
     prof_mark(s, sl, ST_FILTER);
+    lpf::FilterArgs a;
     if (n_rows > 0) {
-        lpf::FilterArgs a;
         a.D = s->D; a.P = s->P; a.H = s->H; a.W = s->W; a.r = s->prm.box_r; a.kappa = s->prm.kappa;
         a.tiles_x = s->tiles_x; a.tiles_y = s->tiles_y;
         a.member_start = s->d_member_start; a.member_ord = s->d_member_ord;
@@ -475,6 +484,14 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
                 lpf::k_filter<8><<<grid, lpf::kFilterThreads, s->filter_smem, s->st>>>(a);
             else
                 lpf::k_filter<16><<<grid, lpf::kFilterThreads, s->filter_smem, s->st>>>(a);
+        }
+    }
+    prof_mark(s, sl, ST_LMAX);
+    if (n_rows > 0 && s->stream_filter) {
+        switch (s->prm.dtype) {
+            case LPF_FP32: launch_lmax_res<float>(s, a, Tmod); break;
+            case LPF_FP16: launch_lmax_res<__half>(s, a, Tmod); break;
+            default: launch_lmax_res<__nv_bfloat16>(s, a, Tmod); break;
         }
     }
     prof_mark(s, sl, ST_SORT);
