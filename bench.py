@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dtype", default="fp32", choices=["fp32", "fp16", "bf16"])
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pool", type=int, default=12, help="distinct synthetic frames cycled")
     ap.add_argument("--workload", default="aartfaac", choices=["aartfaac", "serving"],
@@ -292,7 +292,7 @@ def run_ours(args):
     lat = []
     e2e_cands = []
     t_push = {}
-    depth = max(1, RESULT_SLOTS - 1)
+    inflight = max(1, RESULT_SLOTS - 1)
 
     def poll_host():
         Tp, c, n, _ = s.poll(timeout_ms=600000)
@@ -305,7 +305,7 @@ def run_ours(args):
         t_push[T] = time.perf_counter()
         s.push_host(pool_pin[T % args.pool], T)
         T += 1
-        if len(t_push) >= depth + 1:
+        if len(t_push) >= inflight + 1:
             poll_host()
     while t_push:
         poll_host()

@@ -75,6 +75,18 @@ class LpfError(RuntimeError):
         super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
 
 
+def _host_records(n: int):
+    """A reusable host array of n candidate records and the object owning its memory,
+    page-locked where CUDA can pin it (the poll's device-to-host copy is then one
+    DMA, not a staged copy)."""
+    try:
+        import torch
+        t = torch.empty(n * CANDIDATE_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True)
+        return t.numpy().view(CANDIDATE_DTYPE), t
+    except Exception:
+        return np.zeros(n, dtype=CANDIDATE_DTYPE), None
+
+
 def load(path: Optional[str] = None):
     """Load liblpf.so (building it first if it is missing) and declare its signatures."""
     global _lib
@@ -178,7 +190,7 @@ class Stream:
                                    self.dms.ctypes.data_as(POINTER(c_double)), self.depth,
                                    ctypes.byref(p)), "lpf_stream_open")
         self._h = h
-        self._out = np.zeros(self._cap, dtype=CANDIDATE_DTYPE)
+        self._out, self._out_owner = _host_records(self._cap)
 
     # ---------------------------------------------------------------- pushes
     def push(self, frame, T: int) -> None:

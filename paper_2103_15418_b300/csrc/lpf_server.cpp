@@ -61,7 +61,7 @@ struct ServedStream {
     std::deque<Frame> queued;      // submitted, not yet on the GPU
     std::deque<Frame> inflight;    // pushed, not yet polled
     std::deque<Result> done;       // finished, not yet fetched
-    std::vector<lpf_candidate> poll_buf;   // cand_cap records, reused by every poll
+    lpf_candidate* poll_buf = nullptr;     // pinned, cand_cap records, reused by every poll
     bool close_requested = false;
     int last_rc = LPF_OK;
     std::vector<double> latencies;
@@ -99,6 +99,8 @@ void release_pool(ServedStream* st) {
     for (float* p : st->pool) cudaFreeHost(p);
     st->pool.clear();
     st->free_bufs.clear();
+    if (st->poll_buf) cudaFreeHost(st->poll_buf);
+    st->poll_buf = nullptr;
 }
 
 double percentile(std::vector<double> v, double q) {
@@ -137,9 +139,20 @@ bool tick(lpf_server* srv, std::unique_lock<std::mutex>& lk) {
             release_pool(st);
         } else {
             st->s = s;
-            st->poll_buf.resize((size_t)st->prm.cand_cap);
-            st->state = LPF_SERVE_ACTIVE;
-            srv->used += st->footprint;
+            // pinned, so that the candidate copy of every poll is a plain DMA
+            if (cudaMallocHost((void**)&st->poll_buf, sizeof(lpf_candidate) * (size_t)st->prm.cand_cap) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                st->poll_buf = nullptr;
+                lpf_stream_close(s);
+                st->s = nullptr;
+                st->state = LPF_SERVE_CLOSED;
+                st->last_rc = LPF_E_OOM;
+                release_pool(st);
+            } else {
+                st->state = LPF_SERVE_ACTIVE;
+                srv->used += st->footprint;
+            }
         }
         progress = true;
     }
@@ -168,7 +181,7 @@ bool tick(lpf_server* srv, std::unique_lock<std::mutex>& lk) {
             Result r;
             int n = 0;
             int64_t T = -1;
-            int rc = lpf_poll_candidates(st->s, st->poll_buf.data(), st->prm.cand_cap, &n, &T, 0);
+            int rc = lpf_poll_candidates(st->s, st->poll_buf, st->prm.cand_cap, &n, &T, 0);
             if (rc == LPF_E_TIMEOUT) break;
             Frame fr = st->inflight.front();
             st->inflight.pop_front();
@@ -177,7 +190,7 @@ bool tick(lpf_server* srv, std::unique_lock<std::mutex>& lk) {
             r.rc = rc;
             r.n_found = n;
             r.latency_ms = std::chrono::duration<double, std::milli>(now - fr.submitted).count();
-            r.cands.assign(st->poll_buf.begin(), st->poll_buf.begin() + std::min(n, st->prm.cand_cap));
+            r.cands.assign(st->poll_buf, st->poll_buf + std::min(n, st->prm.cand_cap));
             st->latencies.push_back(r.latency_ms);
             st->frames_done += 1;
             st->last_done = now;
