@@ -254,3 +254,32 @@ def test_host_push_matches_device_push(lib):
             ca = a.poll(timeout_ms=60000)[1]
             cb = b.poll(timeout_ms=60000)[1]
             assert ca.tobytes() == cb.tobytes()
+
+
+def test_crossing_list_overflow_resolves_every_crossing(lib):
+    """kappa = 0.5: about a third of all pixels of every delay row cross the
+    threshold, more than the crossing list holds (max(cand_cap, rows x pixels /
+    32)); the overflowing warps resolve their crossings inside the filter and
+    the candidates and their count still match the oracle exactly."""
+    spec = synth.spec_aartfaac(H=320, W=320, dm_grid=np.arange(64, dtype=np.float64), depth=16,
+                               box_r=7, kappa=0.5, n_sources=10, n_pulses=0, n_frames=20)
+    st = synth.SyntheticStream(spec, seed=21)
+    fa = cached_frames(st)
+    delays = O.delay_table(spec.freqs_mhz, spec.dm_grid, spec.cadence_s)
+    T = int(delays.max()) + 2
+    with _open(lib, spec) as s:
+        for t in range(T + 1):
+            _push(s, st, t)
+            _, c, n, trunc = s.poll(timeout_ms=60000)
+        assert not trunc and n == len(c)
+        assert_sorted_unique(c)
+        n_rows = s.info()["n_distinct"]
+        xcap = max(1 << 20, n_rows * spec.H * spec.W // 32)
+        _, _, maps = O.search_push(fa, T, delays, spec.box_r, spec.kappa, keep_maps=True)
+        rows = {}
+        for d in range(len(delays)):
+            rows.setdefault(tuple(delays[d]), d)
+        crossings = sum(int((maps[d]["snr"] > spec.kappa).sum()) for d in rows.values())
+        assert crossings > xcap, (crossings, xcap)        # the overflow path ran
+        res = compare_push(c, fa, T, delays, spec.box_r, spec.kappa, gpu_stats=s.stats())
+        assert res["matched"] > 100000
