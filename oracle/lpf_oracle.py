@@ -20,6 +20,10 @@ method, each citing the passage of Ruhe et al. (arXiv 2103.15418) it follows:
   search_push_residual  the same search with D - C as a shift-sum of per-subband
                    residuals X - C(X) (linearity of the local centre); reference
                    for rings that store those residuals in reduced precision
+  qc_band_scores   App. A, z = (b - median(b)) / MAD(b) of the band-image means
+  QCState, qc_frame  App. A, per-pixel running mean / standard deviation
+                   (Welford) and scores zeta; bands over either threshold are
+                   imputed with zeros
 
 Readings where the paper is silent or garbled (all listed in the design doc):
   * C_DM = 4.148808e3 s MHz^2 cm^3 / pc (the printed unit "ms" is garbled; with
@@ -34,6 +38,13 @@ Readings where the paper is silent or garbled (all listed in the design doc):
     carry snr = 0.
   * A candidate's t0 is its arrival frame at nu_ref; it is produced by the push
     of frame T = t0 + max_f delay[d][f].
+  * Quality control (App. A): MAD is the median absolute deviation from the
+    median (the text's expansion "mean absolute deviation" is garbled; the
+    statistics are robust ones); both thresholds apply to |z| and |zeta|; the
+    pixel scores use the running statistics before the current frame, with the
+    sample standard deviation, once a band has min_frames frames folded in,
+    and only where that deviation is positive; only kept band images are
+    folded into the running statistics.
 
 Functions with no independent pin: none (see tests/test_oracle_pins.py).
 """
@@ -294,3 +305,68 @@ def storage_round(x: np.ndarray, dtype: str) -> np.ndarray:
     if dtype == "bf16":
         return t.to(torch.bfloat16).double().numpy()
     raise ValueError(dtype)
+
+
+# --------------------------------------------------------------------- quality control
+def qc_band_scores(frame: np.ndarray) -> np.ndarray:
+    """z_b = (b_b - median(b)) / MAD(b) with b_b the mean of band image b (App. A).
+
+    MAD(b) = median(|b - median(b)|).  Where MAD = 0 a band equal to the median
+    scores 0 and any other band +-inf.
+    """
+    F = frame.shape[0]
+    b = np.asarray(frame, np.float64).reshape(F, -1).mean(axis=1)
+    med = np.median(b)
+    mad = np.median(np.abs(b - med))
+    dev = b - med
+    if mad > 0:
+        return dev / mad
+    return np.where(dev == 0, 0.0, np.copysign(np.inf, dev))
+
+
+class QCState:
+    """Running per-pixel statistics of the kept band images (App. A, Welford):
+    per band the number n of frames folded in, per pixel the mean and the sum of
+    squared deviations m2 (sample variance m2 / (n - 1))."""
+
+    def __init__(self, F: int, H: int, W: int):
+        self.n = np.zeros(F, np.int64)
+        self.mean = np.zeros((F, H, W))
+        self.m2 = np.zeros((F, H, W))
+
+
+def qc_pixel_scores(frame: np.ndarray, state: QCState, min_frames: int) -> np.ndarray:
+    """Per band the largest |zeta| = |x - mean| / s over pixels with s > 0, using the
+    statistics before this frame; 0 for a band with fewer than min_frames frames."""
+    F = frame.shape[0]
+    out = np.zeros(F)
+    for f in range(F):
+        n = int(state.n[f])
+        if n < max(min_frames, 2):
+            continue
+        s = np.sqrt(state.m2[f] / (n - 1))
+        ok = s > 0
+        if ok.any():
+            out[f] = float(np.max(np.abs(np.asarray(frame[f], np.float64)[ok] - state.mean[f][ok]) / s[ok]))
+    return out
+
+
+def qc_frame(frame: np.ndarray, state: QCState, z_thr: float, zeta_thr: float, min_frames: int):
+    """Quality control of one image cube (App. A): band image b is discarded
+    (imputed with zeros) when |z_b| > z_thr or any |zeta_bij| > zeta_thr; the
+    kept band images are then folded into the running statistics.
+
+    Returns (frame after imputation, discarded [F] bool, z [F], max |zeta| [F]).
+    """
+    x = np.asarray(frame, np.float64)
+    z = qc_band_scores(x)
+    zeta = qc_pixel_scores(x, state, min_frames)
+    discard = (np.abs(z) > z_thr) | (zeta > zeta_thr)
+    out = x.copy()
+    out[discard] = 0.0
+    for f in np.nonzero(~discard)[0]:
+        state.n[f] += 1
+        delta = x[f] - state.mean[f]
+        state.mean[f] += delta / state.n[f]
+        state.m2[f] += delta * (x[f] - state.mean[f])
+    return out, discard, z, zeta

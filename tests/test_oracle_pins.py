@@ -402,3 +402,109 @@ def test_residual_form_equals_direct_form():
         for d in ma:
             np.testing.assert_allclose(ma[d]["snr"], mb[d]["snr"], rtol=0, atol=1e-9)
             assert abs(sa[d][1] - sb[d][1]) < 1e-12
+
+
+# ----------------------------------------------------------------- quality control (App. A)
+def _bands(means, H=4, W=4):
+    return np.stack([np.full((H, W), float(v)) for v in means])
+
+
+def test_qc_band_scores_closed_forms():
+    """Median and median absolute deviation worked by hand (App. A z-scores)."""
+    # odd count: median 3, |dev| = 2 1 0 1 97 -> MAD 1
+    assert np.allclose(O.qc_band_scores(_bands([1, 2, 3, 4, 100])), [-2, -1, 0, 1, 97])
+    # even count: median 2.5, |dev| = 1.5 .5 .5 1.5 -> MAD 1
+    assert np.allclose(O.qc_band_scores(_bands([1, 2, 3, 4])), [-1.5, -0.5, 0.5, 1.5])
+    # MAD = 0: the bands at the median score 0, the other +inf
+    z = O.qc_band_scores(_bands([5, 5, 5, 9]))
+    assert list(z[:3]) == [0, 0, 0] and z[3] == np.inf
+    # the band mean is over all pixels of the band image
+    f = _bands([0, 0, 0, 0, 0])
+    f[4, 0, 0] = 16.0                        # mean 1 over 16 pixels
+    assert np.allclose(O.qc_band_scores(f), [0, 0, 0, 0, np.inf])
+
+
+def _qc_history(seed=3, T=40, F=6, H=8, W=9):
+    rng = np.random.default_rng(seed)
+    # band levels differ (as real band images do), so noise alone keeps |z| small
+    level = 0.5 * np.arange(F)[:, None, None]
+    frames = [level + rng.standard_normal((F, H, W)) * (1 + 0.1 * np.arange(F))[:, None, None] for _ in range(T)]
+    frames[17][2] += 40.0                    # a corrupted band (global offset)
+    frames[25][4, 3, 3] += 500.0             # an RFI spike in one band
+    return frames
+
+
+def test_qc_running_statistics_equal_batch_statistics():
+    """Welford state = mean and sample variance of exactly the kept band images."""
+    frames = _qc_history()
+    F, H, W = frames[0].shape
+    st = O.QCState(F, H, W)
+    kept = [[] for _ in range(F)]
+    for x in frames:
+        _, disc, _, _ = O.qc_frame(x, st, z_thr=5.0, zeta_thr=20.0, min_frames=10)
+        for f in range(F):
+            if not disc[f]:
+                kept[f].append(x[f])
+    for f in range(F):
+        h = np.array(kept[f])
+        assert st.n[f] == len(h)
+        assert np.allclose(st.mean[f], h.mean(axis=0), atol=1e-12)
+        assert np.allclose(st.m2[f] / (len(h) - 1), h.var(axis=0, ddof=1), atol=1e-11)
+
+
+def test_qc_discards_corrupted_band_and_spike_only():
+    frames = _qc_history()
+    F, H, W = frames[0].shape
+    st = O.QCState(F, H, W)
+    seen = {}
+    for t, x in enumerate(frames):
+        out, disc, z, zeta = O.qc_frame(x, st, z_thr=5.0, zeta_thr=20.0, min_frames=10)
+        seen[t] = disc.copy()
+        assert np.all(out[disc] == 0) and np.array_equal(out[~disc], x[~disc])
+    assert seen[17][2] and seen[17].sum() == 1           # band offset: |z| large
+    assert seen[25][4] and seen[25].sum() == 1           # spike: |zeta| large
+    assert sum(int(v.sum()) for v in seen.values()) == 2  # nothing else
+
+
+def test_qc_pixel_score_uses_the_previous_statistics():
+    """zeta of the spike frame is computed from the 25 frames before it (band 4 of
+    none of them discarded), by hand."""
+    frames = _qc_history()
+    F, H, W = frames[0].shape
+    st = O.QCState(F, H, W)
+    for x in frames[:25]:
+        O.qc_frame(x, st, z_thr=5.0, zeta_thr=20.0, min_frames=10)
+    hist = np.array([x[4] for x in frames[:25]])
+    s = hist.std(axis=0, ddof=1)
+    expect = np.max(np.abs(frames[25][4] - hist.mean(axis=0)) / s)
+    _, _, _, zeta = O.qc_frame(frames[25], st, z_thr=5.0, zeta_thr=20.0, min_frames=10)
+    assert np.isclose(zeta[4], expect, rtol=1e-12)
+    # and below min_frames no band is pixel-tested
+    st2 = O.QCState(F, H, W)
+    for x in frames[:5]:
+        _, _, _, zeta = O.qc_frame(x, st2, z_thr=5.0, zeta_thr=20.0, min_frames=10)
+        assert np.all(zeta == 0)
+
+
+def test_pins_catch_planted_qc_mistakes():
+    # a mean in place of the median moves every score of the worked example
+    def mean_centre(frame):
+        b = frame.reshape(frame.shape[0], -1).mean(axis=1)
+        c = b.mean()
+        return (b - c) / np.median(np.abs(b - c))
+    assert not np.allclose(mean_centre(_bands([1, 2, 3, 4, 100])), [-2, -1, 0, 1, 97])
+
+    # folding the frame in before scoring it hides the spike (the test above would fail)
+    frames = _qc_history()
+    F, H, W = frames[0].shape
+    st = O.QCState(F, H, W)
+    for x in frames[:25]:
+        O.qc_frame(x, st, z_thr=5.0, zeta_thr=20.0, min_frames=10)
+    n, mean, m2 = st.n[4] + 1, st.mean[4].copy(), st.m2[4].copy()
+    x = frames[25][4]
+    d = x - mean
+    mean += d / n
+    m2 += d * (x - mean)
+    zeta_after = np.max(np.abs(x - mean) / np.sqrt(m2 / (n - 1)))
+    _, _, _, zeta = O.qc_frame(frames[25], st, z_thr=5.0, zeta_thr=20.0, min_frames=10)
+    assert zeta[4] > 20.0 and zeta_after < zeta[4] / 1.5
