@@ -74,6 +74,16 @@ typedef struct {
     void*  cuda_stream;   /* cudaStream_t to run on; NULL = a private non-blocking stream    */
     int    filter_impl;   /* 0 = auto (streaming kernel when box_r is 7 or 15, else tiled),
                              1 = tiled kernel, 2 = streaming kernel (box_r 7 or 15 only)      */
+    /* Quality control of every pushed frame before it enters the ring (App. A):
+     * band image f is imputed with zeros when |z_f| > qc_z, z_f = (b_f - median(b))
+     * / MAD(b) over the band-image means b (MAD: median absolute deviation), or
+     * when some pixel has |x - mean| > qc_zeta * s under the running per-pixel
+     * mean and sample deviation s of the kept band images (Welford; tested once
+     * qc_min_frames frames of the band have been kept, where s > 0).             */
+    int    qc;            /* 0 = off, 1 = on                                       default 0     */
+    float  qc_z;          /* band-score threshold (> 0)                            default 5.0   */
+    float  qc_zeta;       /* pixel-score threshold (> 0)                           default 20.0  */
+    int    qc_min_frames; /* kept frames before the pixel test applies (>= 2)      default 128   */
 } lpf_params;
 
 /* One candidate: pixel (y, x) of DM trial dm_idx (index into dm_grid) whose
@@ -211,6 +221,14 @@ int lpf_get_delay_table(const lpf_stream* s, int32_t* out);
 int lpf_get_stats(const lpf_stream* s, double* out);
 
 int lpf_stream_info(const lpf_stream* s, lpf_stream_info_t* out);
+
+/*
+ * Quality control of the most recently polled frame (params.qc = 1): its T, the
+ * bands imputed with zeros (bit f) and, if z is not NULL, the F band scores z_f.
+ * The paper's quality control (App. A).  Errors: LPF_E_ARG (s NULL),
+ * LPF_E_NODATA (qc off, or no frame polled yet).
+ */
+int lpf_get_qc(const lpf_stream* s, int64_t* T_out, uint32_t* discarded, float* z);
 
 /* Wait (without limit) for all work enqueued on the stream. */
 int lpf_stream_sync(lpf_stream* s);

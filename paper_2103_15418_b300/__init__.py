@@ -29,7 +29,7 @@ DTYPES = {"fp32": 0, "fp16": 1, "bf16": 2}
 EXPORTS = [
     "lpf_default_params", "lpf_stream_open", "lpf_push_frame", "lpf_push_frame_host",
     "lpf_poll_candidates", "lpf_extract_dynspec", "lpf_get_delay_table", "lpf_get_stats",
-    "lpf_stream_info", "lpf_stream_sync", "lpf_stream_close", "lpf_strerror",
+    "lpf_stream_info", "lpf_stream_sync", "lpf_stream_close", "lpf_strerror", "lpf_get_qc",
     "lpf_set_profiling", "lpf_get_kernel_times", "lpf_extract_dynspec_static",
     "lpf_stream_footprint", "lpf_server_open", "lpf_server_open_stream", "lpf_server_submit",
     "lpf_server_fetch", "lpf_server_close_stream", "lpf_server_stream_state", "lpf_server_stats",
@@ -41,7 +41,8 @@ SERVE_PENDING, SERVE_ACTIVE, SERVE_CLOSED = 0, 1, 3
 class Params(Structure):
     _fields_ = [("cadence_s", c_double), ("kappa", c_float), ("box_r", c_int), ("lmax_r", c_int),
                 ("dtype", c_int), ("cand_cap", c_int), ("dyn_box_r", c_int),
-                ("result_slots", c_int), ("cuda_stream", c_void_p), ("filter_impl", c_int)]
+                ("result_slots", c_int), ("cuda_stream", c_void_p), ("filter_impl", c_int),
+                ("qc", c_int), ("qc_z", c_float), ("qc_zeta", c_float), ("qc_min_frames", c_int)]
 
 
 class Candidate(Structure):
@@ -107,6 +108,7 @@ def load(path: Optional[str] = None):
     lib.lpf_extract_dynspec.argtypes = [c_void_p, c_void_p, c_int, c_int, c_void_p]
     lib.lpf_get_delay_table.argtypes = [c_void_p, c_void_p]
     lib.lpf_get_stats.argtypes = [c_void_p, c_void_p]
+    lib.lpf_get_qc.argtypes = [c_void_p, POINTER(c_int64), POINTER(ctypes.c_uint32), c_void_p]
     lib.lpf_stream_info.argtypes = [c_void_p, POINTER(StreamInfo)]
     lib.lpf_stream_sync.argtypes = [c_void_p]
     lib.lpf_stream_close.argtypes = [c_void_p]
@@ -138,11 +140,13 @@ def _check(rc: int, what: str):
 
 def make_params(*, cadence_s: float = 1.0, kappa: float = 6.0, box_r: int = 15, dtype: str = "fp32",
                 cand_cap: int = 1 << 20, dyn_box_r: int = 0, result_slots: int = 2,
-                filter_impl: str = "auto") -> "Params":
+                filter_impl: str = "auto", qc: bool = False, qc_z: float = 5.0, qc_zeta: float = 20.0,
+                qc_min_frames: int = 128) -> "Params":
     p = default_params()
     p.cadence_s, p.kappa, p.box_r = cadence_s, kappa, box_r
     p.dtype, p.cand_cap, p.dyn_box_r, p.result_slots = DTYPES[dtype], cand_cap, dyn_box_r, result_slots
     p.filter_impl = {"auto": 0, "tiled": 1, "streaming": 2}[filter_impl]
+    p.qc, p.qc_z, p.qc_zeta, p.qc_min_frames = int(bool(qc)), qc_z, qc_zeta, qc_min_frames
     return p
 
 
@@ -170,16 +174,16 @@ class Stream:
     def __init__(self, H: int, W: int, freqs_mhz, dm_grid, depth: int, *, cadence_s: float = 1.0,
                  kappa: float = 6.0, box_r: int = 15, dtype: str = "fp32", cand_cap: int = 1 << 20,
                  dyn_box_r: int = 0, result_slots: int = 2, cuda_stream=None,
-                 filter_impl: str = "auto"):
+                 filter_impl: str = "auto", qc: bool = False, qc_z: float = 5.0, qc_zeta: float = 20.0,
+                 qc_min_frames: int = 128):
         lib = load()
         self.H, self.W = int(H), int(W)
         self.freqs = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
         self.dms = np.ascontiguousarray(dm_grid, dtype=np.float64)
         self.F, self.n_dm, self.depth = len(self.freqs), len(self.dms), int(depth)
-        p = default_params()
-        p.cadence_s, p.kappa, p.box_r = cadence_s, kappa, box_r
-        p.dtype, p.cand_cap, p.dyn_box_r, p.result_slots = DTYPES[dtype], cand_cap, dyn_box_r, result_slots
-        p.filter_impl = {"auto": 0, "tiled": 1, "streaming": 2}[filter_impl]
+        p = make_params(cadence_s=cadence_s, kappa=kappa, box_r=box_r, dtype=dtype, cand_cap=cand_cap,
+                        dyn_box_r=dyn_box_r, result_slots=result_slots, filter_impl=filter_impl, qc=qc,
+                        qc_z=qc_z, qc_zeta=qc_zeta, qc_min_frames=qc_min_frames)
         if cuda_stream is not None:
             p.cuda_stream = int(getattr(cuda_stream, "cuda_stream", cuda_stream))
         self.params = p
@@ -244,6 +248,16 @@ class Stream:
         out = np.zeros((self.n_dm, 2), dtype=np.float64)
         _check(load().lpf_get_stats(self._h, c_void_p(out.ctypes.data)), "lpf_get_stats")
         return out
+
+    def qc(self):
+        """Quality control of the last polled frame: (T, discarded [F] bool, z [F])."""
+        T = c_int64(-1)
+        m = ctypes.c_uint32(0)
+        z = np.zeros(self.F, dtype=np.float32)
+        _check(load().lpf_get_qc(self._h, ctypes.byref(T), ctypes.byref(m), c_void_p(z.ctypes.data)),
+               "lpf_get_qc")
+        disc = np.array([(m.value >> f) & 1 for f in range(self.F)], dtype=bool)
+        return T.value, disc, z
 
     def info(self) -> Dict[str, int]:
         i = StreamInfo()

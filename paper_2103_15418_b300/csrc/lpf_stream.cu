@@ -10,6 +10,7 @@
 #include "lpf_kernels.cuh"
 #include "lpf_dedisperse.cuh"
 #include "lpf_residual.cuh"
+#include "lpf_qc.cuh"
 
 #include <algorithm>
 #include <chrono>
@@ -43,6 +44,7 @@ struct Slot {
     int n_active = 0;
     lpf::CandidateRec* d_out = nullptr;
     double* d_stats = nullptr;     // [n_distinct][3]
+    lpf::QcRecord* d_qc = nullptr; // quality-control record of the frame (qc on)
     cudaEvent_t done = nullptr;
 };
 
@@ -95,6 +97,17 @@ struct lpf_stream {
 
     // host pinned
     unsigned* h_count = nullptr;     // [slots]
+    // quality control (App. A), when prm.qc: running per-pixel statistics of the
+    // kept band images and the scratch of the three QC launches
+    float* qc_mean = nullptr;        // [F][P]
+    float* qc_m2 = nullptr;          // [F][P] sum of squared deviations
+    int* qc_n = nullptr;             // [F] frames folded in
+    float* qc_invn = nullptr;        // [F] 1/n of this frame's update
+    double* qc_part = nullptr;       // [F][kQcScanBlocks] band sums
+    unsigned* qc_words = nullptr;    // [2] pixel flags, discard mask
+    lpf::QcRecord* h_qc = nullptr;   // [slots] pinned
+    lpf::QcRecord last_qc{};
+    int64_t last_qc_T = -1;
     double* h_stats = nullptr;       // [slots][n_distinct][3]
 
     cudaStream_t st = nullptr;
@@ -168,6 +181,14 @@ void free_all(lpf_stream* s) {
         for (auto& e : row)
             if (e) cudaEventDestroy(e);
     if (s->h_count) cudaFreeHost(s->h_count);
+    if (s->h_qc) cudaFreeHost(s->h_qc);
+    {
+        void* q[] = {s->qc_mean, s->qc_m2, s->qc_n, s->qc_invn, s->qc_part, s->qc_words};
+        for (void* p : q)
+            if (p) cudaFree(p);
+        for (int i = 0; i < kMaxSlots; ++i)
+            if (s->slots[i].d_qc) cudaFree(s->slots[i].d_qc);
+    }
     if (s->h_stats) cudaFreeHost(s->h_stats);
     for (int i = 0; i < 2; ++i) {
         if (s->stage_ready[i]) cudaEventDestroy(s->stage_ready[i]);
@@ -283,7 +304,11 @@ void launch_ingest(lpf_stream* s, const float* frame, int64_t slot) {
     int vec = ((reinterpret_cast<uintptr_t>(frame) & 15u) == 0 && (s->HW % 4) == 0) ? 1 : 0;
     int64_t work = vec ? s->F * s->HW / 4 : s->F * s->HW;
     int blocks = (int)std::min<int64_t>((work + 255) / 256, 148 * 16);
-    lpf::k_ingest<TS><<<blocks, 256, 0, s->st>>>(frame, dst, s->F, s->HW, s->P, vec);
+    if (s->prm.qc)
+        lpf::k_ingest_qc<TS><<<blocks, 256, 0, s->st>>>(frame, dst, s->F, s->HW, s->P, vec, s->qc_words + 1,
+                                                         s->qc_invn, s->qc_mean, s->qc_m2);
+    else
+        lpf::k_ingest<TS><<<blocks, 256, 0, s->st>>>(frame, dst, s->F, s->HW, s->P, vec);
 }
 
 template <typename TS>
@@ -443,6 +468,13 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
     cudaGetLastError();
 
     prof_mark(s, sl, ST_INGEST);
+    if (s->prm.qc) {
+        lpf::k_qc_scan<<<dim3(lpf::kQcScanBlocks, s->F), 256, 0, s->st>>>(
+            frame_dev, s->HW, s->qc_mean, s->qc_m2, s->qc_n, s->P, s->prm.qc_min_frames, s->prm.qc_zeta,
+            s->qc_part, s->qc_words);
+        lpf::k_qc_decide<<<1, 32, 0, s->st>>>(s->qc_part, s->F, s->HW, s->prm.qc_z, s->qc_words, s->qc_n,
+                                              s->qc_invn, s->qc_words + 1, slot.d_qc);
+    }
     switch (s->prm.dtype) {
         case LPF_FP32: launch_ingest<float>(s, frame_dev, ring_slot); break;
         case LPF_FP16: launch_ingest<__half>(s, frame_dev, ring_slot); break;
@@ -514,6 +546,8 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
     prof_mark(s, sl, ST_N);
     if (cudaGetLastError() != cudaSuccess) return LPF_E_CUDA;
     LPF_TRY(cudaMemcpyAsync(s->h_count + sl, s->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st));
+    if (s->prm.qc)
+        LPF_TRY(cudaMemcpyAsync(s->h_qc + sl, slot.d_qc, sizeof(lpf::QcRecord), cudaMemcpyDeviceToHost, s->st));
     if (n_rows > 0)
         LPF_TRY(cudaMemcpyAsync(s->h_stats + (size_t)sl * s->n_distinct * 3, slot.d_stats,
                                 (size_t)n_rows * 3 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
@@ -555,6 +589,10 @@ void lpf_default_params(lpf_params* p) {
     p->result_slots = 2;
     p->cuda_stream = nullptr;
     p->filter_impl = 0;
+    p->qc = 0;
+    p->qc_z = 5.0f;
+    p->qc_zeta = 20.0f;
+    p->qc_min_frames = 128;
 }
 
 const char* lpf_strerror(int code) {
@@ -597,6 +635,10 @@ int plan_stream(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, 
     if (!std::isfinite(prm.kappa)) return LPF_E_ARG;
     if (prm.filter_impl < 0 || prm.filter_impl > 2) return LPF_E_ARG;
     if (prm.filter_impl == 2 && prm.box_r != 7 && prm.box_r != 15) return LPF_E_ARG;
+    if (prm.qc != 0 && prm.qc != 1) return LPF_E_ARG;
+    if (prm.qc && (!(prm.qc_z > 0) || !(prm.qc_zeta > 0) || !std::isfinite(prm.qc_z) ||
+                   !std::isfinite(prm.qc_zeta) || prm.qc_min_frames < 2))
+        return LPF_E_ARG;
     for (int f = 0; f < F; ++f)
         if (!(freqs_mhz[f] > 0) || !std::isfinite(freqs_mhz[f])) return LPF_E_ARG;
     for (int d = 0; d < n_dm; ++d)
@@ -647,6 +689,11 @@ size_t footprint_bytes(const lpf_stream* s) {
     size_t t = (size_t)s->depth * s->F * s->P * s->elem * (s->stream_filter ? 2 : 1);
     t += b(nd * s->P * 4) + b(2 * (size_t)s->F * s->HW * 4) + b(nd * s->F * 2) + b(nd * 4);
     if (s->xcap > 0) t += b((size_t)s->xcap * 8) + b((size_t)s->xcap * 4);
+    if (s->prm.qc) {
+        t += 2 * b((size_t)s->F * s->P * 4) + b((size_t)s->F * 4) + b((size_t)s->F * 4) +
+             b((size_t)s->F * lpf::kQcScanBlocks * 8) + b(2 * 4);
+        t += (size_t)s->n_slots * b(sizeof(lpf::QcRecord));
+    }
     t += b(s->member_start.size() * 4) + b(s->member_ord.size() * 4) + 2 * b((size_t)s->n_dm * 4);
     t += 2 * (b(cap * 8) + b(cap * 4)) + b(16) + b((size_t)256 * kSortBlocks * 4);
     t += b(nd * n_filter_blocks(s) * 3 * 8);
@@ -737,6 +784,24 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
         if (rc == LPF_OK && cudaEventCreateWithFlags(&s->slots[i].done, cudaEventDisableTiming) != cudaSuccess)
             rc = LPF_E_CUDA;
     }
+    if (prm.qc) {
+        if (rc == LPF_OK) rc = dev_alloc(s, &s->qc_mean, (size_t)F * s->P);
+        if (rc == LPF_OK) rc = dev_alloc(s, &s->qc_m2, (size_t)F * s->P);
+        if (rc == LPF_OK) rc = dev_alloc(s, &s->qc_n, (size_t)F);
+        if (rc == LPF_OK) rc = dev_alloc(s, &s->qc_invn, (size_t)F);
+        if (rc == LPF_OK) rc = dev_alloc(s, &s->qc_part, (size_t)F * lpf::kQcScanBlocks);
+        if (rc == LPF_OK) rc = dev_alloc(s, &s->qc_words, 2);
+        for (int i = 0; i < s->n_slots && rc == LPF_OK; ++i) rc = dev_alloc(s, &s->slots[i].d_qc, 1);
+        if (rc == LPF_OK && (cudaMemsetAsync(s->qc_mean, 0, (size_t)F * s->P * 4, s->st) != cudaSuccess ||
+                             cudaMemsetAsync(s->qc_m2, 0, (size_t)F * s->P * 4, s->st) != cudaSuccess ||
+                             cudaMemsetAsync(s->qc_n, 0, (size_t)F * 4, s->st) != cudaSuccess ||
+                             cudaMemsetAsync(s->qc_words, 0, 2 * 4, s->st) != cudaSuccess))
+            rc = LPF_E_CUDA;
+        if (rc == LPF_OK && cudaMallocHost(&s->h_qc, sizeof(lpf::QcRecord) * kMaxSlots) != cudaSuccess) {
+            cudaGetLastError();
+            rc = LPF_E_OOM;
+        }
+    }
     for (int k = 0; k < s->n_slots && rc == LPF_OK; ++k)
         for (int i = 0; i <= ST_N && rc == LPF_OK; ++i)
             if (cudaEventCreate(&s->ev[k][i]) != cudaSuccess) rc = LPF_E_CUDA;
@@ -826,6 +891,10 @@ int lpf_poll_candidates(lpf_stream* s, lpf_candidate* out_host, int cap, int* n_
         std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
     prof_collect(s, sl);
+    if (s->prm.qc) {
+        s->last_qc = s->h_qc[sl];
+        s->last_qc_T = slot.T;
+    }
     const unsigned found = s->h_count[sl];
     const unsigned stored = std::min<unsigned>(found, (unsigned)s->prm.cand_cap);
     const unsigned ncopy = std::min<unsigned>(stored, (unsigned)cap);
@@ -904,6 +973,15 @@ int lpf_get_stats(const lpf_stream* s, double* out) {
     if (!s || !out) return LPF_E_ARG;
     if (!s->polled) return LPF_E_NODATA;
     std::memcpy(out, s->last_stats.data(), s->last_stats.size() * sizeof(double));
+    return LPF_OK;
+}
+
+int lpf_get_qc(const lpf_stream* s, int64_t* T_out, uint32_t* discarded, float* z) {
+    if (!s) return LPF_E_ARG;
+    if (!s->prm.qc || s->last_qc_T < 0) return LPF_E_NODATA;
+    if (T_out) *T_out = s->last_qc_T;
+    if (discarded) *discarded = s->last_qc.discarded;
+    if (z) std::memcpy(z, s->last_qc.z, sizeof(float) * s->F);
     return LPF_OK;
 }
 

@@ -36,6 +36,8 @@ def test_struct_layouts():
     p = lpf.default_params()
     assert (p.cadence_s, p.kappa, p.box_r, p.lmax_r, p.dtype) == (1.0, 6.0, 15, 1, 0)
     assert p.cand_cap == 1 << 20 and p.result_slots == 2 and not p.cuda_stream
+    # the fields after the pointer read back the library's defaults: same layout
+    assert (p.filter_impl, p.qc, p.qc_z, p.qc_zeta, p.qc_min_frames) == (0, 0, 5.0, 20.0, 128)
 
 
 def test_strerror_names_every_code():
@@ -56,6 +58,9 @@ def test_argument_validation_before_any_cuda_call():
         dict(H=8, W=8, freqs_mhz=f, dm_grid=dm, depth=8, box_r=0),
         dict(H=8, W=8, freqs_mhz=f, dm_grid=dm, depth=8, cadence_s=0.0),
         dict(H=8, W=8, freqs_mhz=f, dm_grid=dm, depth=8, result_slots=0),
+        dict(H=8, W=8, freqs_mhz=f, dm_grid=dm, depth=8, qc=True, qc_z=0.0),
+        dict(H=8, W=8, freqs_mhz=f, dm_grid=dm, depth=8, qc=True, qc_zeta=-1.0),
+        dict(H=8, W=8, freqs_mhz=f, dm_grid=dm, depth=8, qc=True, qc_min_frames=1),
     ]
     for kw in bad:
         with pytest.raises(lpf.LpfError) as e:
@@ -69,6 +74,7 @@ def test_argument_validation_before_any_cuda_call():
 
 def test_null_handles_are_rejected():
     lib = lpf.load()
+    assert lib.lpf_get_qc(None, None, None, None) == lpf.LPF_E_ARG
     assert lib.lpf_push_frame(None, None, 0) == lpf.LPF_E_ARG
     assert lib.lpf_poll_candidates(None, None, 0, None, None, 0) == lpf.LPF_E_ARG
     assert lib.lpf_stream_close(None) == lpf.LPF_OK
@@ -106,3 +112,14 @@ def test_stress_config_depth_96_is_rejected():
     assert e.value.code == lpf.LPF_E_DEPTH
     fp = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, 114, dtype="fp16")
     assert 72e9 < fp < 80e9        # 2 x 30.6 GB rings (raw, residual) + 13.8 GB images of D - C
+
+
+def test_quality_control_footprint():
+    """Quality control adds the running mean and m2 planes ([F][P] FP32 each) and a
+    few hundred bytes of scratch per stream."""
+    import synth
+    sp = synth.spec_aartfaac(H=256, W=256)
+    off = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth)
+    on = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth, qc=True)
+    planes = 2 * sp.F * sp.H * sp.W * 4
+    assert planes < on - off < planes + 64 * 1024
