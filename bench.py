@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pool", type=int, default=12, help="distinct synthetic frames cycled")
+    ap.add_argument("--qc", action="store_true",
+                    help="quality control of every frame before the search (band and pixel scores)")
     ap.add_argument("--workload", default="aartfaac", choices=["aartfaac", "serving"],
                     help="serving: four concurrent FP16 streams through the C++ serving loop")
     ap.add_argument("--cadence", type=float, default=1.0, help="serving: frame cadence in seconds")
@@ -236,7 +238,8 @@ def run_ours(args):
     pool_pin = [p.pin_memory() for p in pool]
     cur = torch.cuda.current_stream(dev)
     s = lpf.Stream(spec.H, spec.W, spec.freqs_mhz, spec.dm_grid, spec.depth, kappa=spec.kappa,
-                   box_r=spec.box_r, dtype=args.dtype, result_slots=RESULT_SLOTS, cuda_stream=cur)
+                   box_r=spec.box_r, dtype=args.dtype, result_slots=RESULT_SLOTS, cuda_stream=cur,
+                   qc=args.qc, qc_min_frames=16)
     info = s.info()
     delays = s.delay_table()
     nbytes = algorithmic_bytes(spec, delays, info["n_distinct"])
@@ -349,6 +352,16 @@ def run_ours(args):
               "traffic": traffic.get("k_filter_res"),
               "algorithmic_flop_per_launch": f_ops, "avg_launch_ms": f_ms, "launches_per_step": 1}
     roof = roof_f if f_ms >= dd_ms else roof_dd
+    # quality control + ingest (k_qc_scan, k_qc_decide, k_ingest_qc, k_residual): the
+    # QC passes read the frame and the running mean and m2 twice and write them once
+    b = 4 if args.dtype == "fp32" else 2
+    qc_bytes = spec.F * HW * (12 + 20 + b)
+    qc_ms = per_push["ingest"]
+    roof_qc = {"kernel": "quality control + ingest (k_qc_scan, k_qc_decide, k_ingest_qc, k_residual)",
+               "bound": "hbm", "achieved": qc_bytes / (qc_ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+               "frac": qc_bytes / (qc_ms / 1e3) / 1e9 / hbm_peak, "peak_source": peak_src, "traffic": None,
+               "algorithmic_bytes_per_launch": qc_bytes, "avg_launch_ms": qc_ms, "launches_per_step": 1,
+               "note": "the stage also runs k_residual (per-subband X - C(X)), not counted in the bytes"}
     path_ach = nbytes["path"] / (elapsed / args.steps) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
@@ -359,6 +372,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "H": spec.H, "W": spec.W, "subbands": spec.F,
                    "dm_trials": spec.n_dm, "depth": depth, "box": 2 * spec.box_r + 1,
                    "storage": args.dtype, "distinct_delay_rows": info["n_distinct"],
+                   "quality_control": bool(args.qc),
                    "l2": "inputs larger than L2 (ring %.2f GB)" % (info["ring_bytes"] / 1e9),
                    "parallelism": f"{ws} independent stream(s), one per GPU"},
         "e2e": {"value": e2e_value, "unit": METRIC,
@@ -369,9 +383,9 @@ def run_ours(args):
                        "what": f"push_frame_host -> poll of the same frame, up to {RESULT_SLOTS} frames in flight"},
         # per push: ingest + residual, counter reset, shift-sum, filter, 3x3 maximum,
         # 3 per sort pass, format, stats
-        "gpu_launches": int(args.steps * (8 + 3 * _passes(spec))),
+        "gpu_launches": int(args.steps * (8 + 3 * _passes(spec) + (2 if args.qc else 0))),
         "roofline": roof,
-        "rooflines": [roof_f, roof_dd],
+        "rooflines": [roof_f, roof_dd] + ([roof_qc] if args.qc else []),
         "path_roofline": {"bound": "hbm", "achieved": path_ach, "peak": hbm_peak, "unit": "GB/s",
                           "frac": path_ach / hbm_peak,
                           "algorithmic_bytes_per_step": nbytes["path"],
