@@ -20,6 +20,7 @@ method, each citing the passage of Ruhe et al. (arXiv 2103.15418) it follows:
   search_push_residual  the same search with D - C as a shift-sum of per-subband
                    residuals X - C(X) (linearity of the local centre); reference
                    for rings that store those residuals in reduced precision
+  subband_detect   Sec. 2.1.1-2.1.2 on every band image, (2k+1)^2 maximum (k = 3)
   qc_band_scores   App. A, z = (b - median(b)) / MAD(b) of the band-image means
   QCState, qc_frame  App. A, per-pixel running mean / standard deviation
                    (Welford) and scores zeta; bands over either threshold are
@@ -162,34 +163,36 @@ def snr_map(D: np.ndarray, C: np.ndarray, S: np.ndarray) -> np.ndarray:
     return out
 
 
-def neighbour_max(D: np.ndarray) -> np.ndarray:
-    """Max of the 8 neighbours inside the image (-inf where there are none)."""
+def neighbour_max(D: np.ndarray, k: int = 1) -> np.ndarray:
+    """Max of the other pixels of the (2k+1)^2 window inside the image (-inf where
+    there are none)."""
     H, W = D.shape
-    pad = np.full((H + 2, W + 2), -np.inf)
-    pad[1:-1, 1:-1] = D
+    pad = np.full((H + 2 * k, W + 2 * k), -np.inf)
+    pad[k:k + H, k:k + W] = D
     best = np.full((H, W), -np.inf)
-    for dy in (-1, 0, 1):
-        for dx in (-1, 0, 1):
+    for dy in range(-k, k + 1):
+        for dx in range(-k, k + 1):
             if dy == 0 and dx == 0:
                 continue
-            best = np.maximum(best, pad[1 + dy:1 + dy + H, 1 + dx:1 + dx + W])
+            best = np.maximum(best, pad[k + dy:k + dy + H, k + dx:k + dx + W])
     return best
 
 
-def local_max_mask(D: np.ndarray) -> np.ndarray:
-    """q = I(D = max over the 3x3 window clipped to the image) (Sec. 2.1.2, k = 1)."""
-    return D >= neighbour_max(D)
+def local_max_mask(D: np.ndarray, k: int = 1) -> np.ndarray:
+    """q = I(D = max over the (2k+1)^2 window clipped to the image) (Sec. 2.1.2;
+    the dispersed search uses k = 1, the paper's per-subband detector k = 3)."""
+    return D >= neighbour_max(D, k)
 
 
-def detect(D: np.ndarray, r: int, kappa: float) -> Dict[str, np.ndarray]:
+def detect(D: np.ndarray, r: int, kappa: float, k: int = 1) -> Dict[str, np.ndarray]:
     """Full per-image chain: C, S, snr, threshold AND local max (Sec. 2.1.1-2.1.2)."""
     C = local_centre(D, r)
     S = local_spread(D, C, r)
     snr = snr_map(D, C, S)
     above = snr > kappa                     # y: x > c + kappa sqrt(s), S > 0
-    q = local_max_mask(D)
+    q = local_max_mask(D, k)
     return dict(C=C, S=S, snr=snr, valid=S > 0, mask=above & q & (S > 0),
-                lmax_margin=D - neighbour_max(D))
+                lmax_margin=D - neighbour_max(D, k))
 
 
 # --------------------------------------------------------------------- a7
@@ -370,3 +373,25 @@ def qc_frame(frame: np.ndarray, state: QCState, z_thr: float, zeta_thr: float, m
         state.mean[f] += delta / state.n[f]
         state.m2[f] += delta * (x[f] - state.mean[f])
     return out, discard, z, zeta
+
+
+# --------------------------------------------------------------------- per-subband detector
+def subband_detect(frame: np.ndarray, r: int, kappa: float, k: int = 3):
+    """The paper's per-bandpass detector on one image cube (Sec. 2.1.1-2.1.2): the
+    one-pass centre / spread filter and threshold on every band image X_b, the
+    (2k+1)^2 maximum filter on X_b (k = 3 in the paper), P_b = q AND y.
+
+    Returns (cands sorted by (b, y, x) as (b, y, x, snr), stats b -> (mean, rms, n),
+    maps b -> detect() dict).
+    """
+    x = np.asarray(frame, np.float64)
+    cands, stats, maps = [], {}, {}
+    for b in range(x.shape[0]):
+        res = detect(x[b], r, kappa, k)
+        ys, xs = np.nonzero(res["mask"])
+        for y, xx in zip(ys, xs):
+            cands.append((b, int(y), int(xx), float(res["snr"][y, xx])))
+        stats[b] = frame_stats(res["snr"], res["valid"])
+        maps[b] = res
+    cands.sort(key=lambda c: (c[0], c[1], c[2]))
+    return cands, stats, maps

@@ -47,14 +47,14 @@ def brute_spread(img, C, r):
     return out
 
 
-def brute_local_max(img):
+def brute_local_max(img, k=1):
     H, W = img.shape
     out = np.zeros((H, W), bool)
     for y in range(H):
         for x in range(W):
             m = -math.inf
-            for yy in range(y - 1, y + 2):
-                for xx in range(x - 1, x + 2):
+            for yy in range(y - k, y + k + 1):
+                for xx in range(x - k, x + k + 1):
                     if 0 <= yy < H and 0 <= xx < W:
                         m = max(m, img[yy, xx])
             out[y, x] = img[y, x] == m
@@ -508,3 +508,51 @@ def test_pins_catch_planted_qc_mistakes():
     zeta_after = np.max(np.abs(x - mean) / np.sqrt(m2 / (n - 1)))
     _, _, _, zeta = O.qc_frame(frames[25], st, z_thr=5.0, zeta_thr=20.0, min_frames=10)
     assert zeta[4] > 20.0 and zeta_after < zeta[4] / 1.5
+
+
+
+# ----------------------------------------------------------------- per-subband detector (Sec. 2.1.1-2.1.2)
+def test_local_max_radius_3_matches_brute_force():
+    rng = np.random.default_rng(15)
+    img = rng.integers(0, 6, (17, 14)).astype(float)     # ties and clipped windows
+    assert np.array_equal(O.local_max_mask(img, 3), brute_local_max(img, 3))
+    assert np.array_equal(O.local_max_mask(img, 1), brute_local_max(img, 1))
+
+
+def test_iid_noise_local_max_fraction_radius_3_is_one_49th():
+    rng = np.random.default_rng(16)
+    img = rng.standard_normal((600, 600))
+    frac = O.local_max_mask(img, 3)[3:-3, 3:-3].mean()
+    n = 594 * 594
+    sigma = math.sqrt((1 / 49) * (48 / 49) / n) * 7     # overlapping windows are dependent
+    assert abs(frac - 1 / 49) < 5 * sigma
+
+
+def test_subband_detect_finds_a_source_in_one_band_only():
+    """A compact source in band 2 only (31x31 box, so its own flux does not swamp
+    its spread): one candidate there, none in the other bands.  A side lobe 3 px
+    away is above the threshold and a 3x3 maximum, but the 7x7 maximum filter
+    merges it into the source (the deblending of Sec. 2.1.2)."""
+    rng = np.random.default_rng(17)
+    F, H, W = 4, 48, 48
+    x = rng.standard_normal((F, H, W)) * 0.1
+    yy, xx = np.mgrid[:H, :W]
+    x[2] += 20.0 * np.exp(-((yy - 20) ** 2 + (xx - 30) ** 2) / (2 * 1.5 ** 2))
+    x[2, 20, 33] += 14.0                                # the side lobe
+    cands, stats, maps = O.subband_detect(x, 15, 6.0, k=3)
+    assert [(b, y, xq) for b, y, xq, _ in cands] == [(2, 20, 30)]
+    three = O.detect(x[2], 15, 6.0, 1)
+    assert three["mask"][20, 33] and three["mask"][20, 30]   # the 3x3 window keeps both
+    assert set(stats) == {0, 1, 2, 3}
+
+
+def test_subband_detect_is_detect_per_band():
+    rng = np.random.default_rng(18)
+    x = rng.standard_normal((3, 20, 24))
+    x[1, 5, 7] += 30.0
+    cands, _, maps = O.subband_detect(x, 5, 4.0, k=2)
+    for b in range(3):
+        ref = O.detect(x[b], 5, 4.0, 2)
+        assert np.array_equal(maps[b]["mask"], ref["mask"])
+        got = sorted((y, xq) for bb, y, xq, _ in cands if bb == b)
+        assert got == sorted(zip(*np.nonzero(ref["mask"])))
