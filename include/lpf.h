@@ -55,6 +55,10 @@ extern "C" {
 #define LPF_E_NODATA    -11   /* poll with no pushed-and-unpolled frame                  */
 #define LPF_E_CAPACITY  -12   /* request larger than a fixed-capacity staging area       */
 
+/* what a stream computes per pushed frame */
+#define LPF_MODE_DISPERSED 0   /* the dispersed-transient search over the DM trials (Sec. 2.1, App. B.2) */
+#define LPF_MODE_SUBBAND   1   /* the per-subband detector: every band image of the frame (Sec. 2.1.1-2.1.2) */
+
 /* storage type of the ring buffer (arithmetic is always FP32) */
 #define LPF_FP32 0
 #define LPF_FP16 1
@@ -66,7 +70,8 @@ typedef struct {
     double cadence_s;     /* frame cadence in seconds (> 0)                     default 1.0   */
     float  kappa;         /* S/N threshold (strict >)                            default 6.0   */
     int    box_r;         /* background box radius r, window (2r+1)^2, 1..16      default 15    */
-    int    lmax_r;        /* local-maximum radius; only 1 (3x3) is supported      default 1     */
+    int    lmax_r;        /* local-maximum radius: 1 (3x3) for the dispersed search;
+                             1..3 for the per-subband detector (3: the paper's 7x7)  default 1 */
     int    dtype;         /* LPF_FP32 / LPF_FP16 / LPF_BF16 ring storage          default FP32  */
     int    cand_cap;      /* device candidate capacity per frame (records)       default 1<<20 */
     int    dyn_box_r;     /* dynspec box radius (0 = the candidate pixel)         default 0     */
@@ -84,6 +89,12 @@ typedef struct {
     float  qc_z;          /* band-score threshold (> 0)                            default 5.0   */
     float  qc_zeta;       /* pixel-score threshold (> 0)                           default 20.0  */
     int    qc_min_frames; /* kept frames before the pixel test applies (>= 2)      default 128   */
+    /* LPF_MODE_SUBBAND: each push detects sources in every band image X_f of the
+     * frame itself (the one-pass centre/spread filter with box_r 7 or 15, the
+     * threshold, the (2 lmax_r + 1)^2 maximum filter on X_f).  n_dm and dm_grid of
+     * lpf_stream_open are then ignored (0 and NULL allowed); a candidate's dm_idx
+     * is its band f and t0 its frame T; lpf_get_stats has one row per band.     */
+    int    mode;          /* LPF_MODE_DISPERSED / LPF_MODE_SUBBAND                 default DISPERSED */
 } lpf_params;
 
 /* One candidate: pixel (y, x) of DM trial dm_idx (index into dm_grid) whose

@@ -36,13 +36,15 @@ EXPORTS = [
     "lpf_server_close",
 ]
 SERVE_PENDING, SERVE_ACTIVE, SERVE_CLOSED = 0, 1, 3
+MODES = {"dispersed": 0, "subband": 1}
 
 
 class Params(Structure):
     _fields_ = [("cadence_s", c_double), ("kappa", c_float), ("box_r", c_int), ("lmax_r", c_int),
                 ("dtype", c_int), ("cand_cap", c_int), ("dyn_box_r", c_int),
                 ("result_slots", c_int), ("cuda_stream", c_void_p), ("filter_impl", c_int),
-                ("qc", c_int), ("qc_z", c_float), ("qc_zeta", c_float), ("qc_min_frames", c_int)]
+                ("qc", c_int), ("qc_z", c_float), ("qc_zeta", c_float), ("qc_min_frames", c_int),
+                ("mode", c_int)]
 
 
 class Candidate(Structure):
@@ -141,23 +143,25 @@ def _check(rc: int, what: str):
 def make_params(*, cadence_s: float = 1.0, kappa: float = 6.0, box_r: int = 15, dtype: str = "fp32",
                 cand_cap: int = 1 << 20, dyn_box_r: int = 0, result_slots: int = 2,
                 filter_impl: str = "auto", qc: bool = False, qc_z: float = 5.0, qc_zeta: float = 20.0,
-                qc_min_frames: int = 128) -> "Params":
+                qc_min_frames: int = 128, mode: str = "dispersed", lmax_r: int = 1) -> "Params":
     p = default_params()
     p.cadence_s, p.kappa, p.box_r = cadence_s, kappa, box_r
     p.dtype, p.cand_cap, p.dyn_box_r, p.result_slots = DTYPES[dtype], cand_cap, dyn_box_r, result_slots
     p.filter_impl = {"auto": 0, "tiled": 1, "streaming": 2}[filter_impl]
     p.qc, p.qc_z, p.qc_zeta, p.qc_min_frames = int(bool(qc)), qc_z, qc_zeta, qc_min_frames
+    p.mode, p.lmax_r = MODES[mode], lmax_r
     return p
 
 
 def footprint(H: int, W: int, freqs_mhz, dm_grid, depth: int, **kw) -> int:
     """Device bytes a stream with these arguments allocates (host-side plan, no GPU)."""
     f = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
-    d = np.ascontiguousarray(dm_grid, dtype=np.float64)
+    d = np.zeros(0) if dm_grid is None else np.ascontiguousarray(dm_grid, dtype=np.float64)
     p = make_params(**kw)
     out = c_size_t(0)
     _check(load().lpf_stream_footprint(int(H), int(W), len(f), f.ctypes.data_as(POINTER(c_double)), len(d),
-                                       d.ctypes.data_as(POINTER(c_double)), int(depth), ctypes.byref(p),
+                                       d.ctypes.data_as(POINTER(c_double)) if len(d) else None, int(depth),
+                                       ctypes.byref(p),
                                        ctypes.byref(out)), "lpf_stream_footprint")
     return int(out.value)
 
@@ -175,24 +179,29 @@ class Stream:
                  kappa: float = 6.0, box_r: int = 15, dtype: str = "fp32", cand_cap: int = 1 << 20,
                  dyn_box_r: int = 0, result_slots: int = 2, cuda_stream=None,
                  filter_impl: str = "auto", qc: bool = False, qc_z: float = 5.0, qc_zeta: float = 20.0,
-                 qc_min_frames: int = 128):
+                 qc_min_frames: int = 128, mode: str = "dispersed", lmax_r: int = 1):
+        """mode "subband": the per-subband detector (dm_grid ignored, may be None; a
+        candidate's dm_idx is its band, t0 its frame; lmax_r 3 gives the paper's 7x7
+        maximum filter)."""
         lib = load()
         self.H, self.W = int(H), int(W)
         self.freqs = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
-        self.dms = np.ascontiguousarray(dm_grid, dtype=np.float64)
-        self.F, self.n_dm, self.depth = len(self.freqs), len(self.dms), int(depth)
+        band = mode == "subband"
+        self.dms = np.zeros(0) if band else np.ascontiguousarray(dm_grid, dtype=np.float64)
+        self.F, self.depth = len(self.freqs), int(depth)
+        self.n_dm = self.F if band else len(self.dms)
         p = make_params(cadence_s=cadence_s, kappa=kappa, box_r=box_r, dtype=dtype, cand_cap=cand_cap,
                         dyn_box_r=dyn_box_r, result_slots=result_slots, filter_impl=filter_impl, qc=qc,
-                        qc_z=qc_z, qc_zeta=qc_zeta, qc_min_frames=qc_min_frames)
+                        qc_z=qc_z, qc_zeta=qc_zeta, qc_min_frames=qc_min_frames, mode=mode, lmax_r=lmax_r)
         if cuda_stream is not None:
             p.cuda_stream = int(getattr(cuda_stream, "cuda_stream", cuda_stream))
         self.params = p
         self._cap = int(cand_cap)
         h = c_void_p()
         _check(lib.lpf_stream_open(ctypes.byref(h), self.H, self.W, self.F,
-                                   self.freqs.ctypes.data_as(POINTER(c_double)), self.n_dm,
-                                   self.dms.ctypes.data_as(POINTER(c_double)), self.depth,
-                                   ctypes.byref(p)), "lpf_stream_open")
+                                   self.freqs.ctypes.data_as(POINTER(c_double)), len(self.dms),
+                                   self.dms.ctypes.data_as(POINTER(c_double)) if len(self.dms) else None,
+                                   self.depth, ctypes.byref(p)), "lpf_stream_open")
         self._h = h
         self._out, self._out_owner = _host_records(self._cap)
 

@@ -133,6 +133,7 @@ struct ResArgs {
     float* xvals;            // ... and their S/N
     unsigned long long* xcounter;   // crossings reserved (may exceed xcap)
     int64_t xcap;            // crossing list capacity
+    int band_k;              // per-subband detector: local-maximum radius k on X_row (0: dispersed search)
 };
 
 // a crossing slot reserved by a warp that resolved its crossings itself
@@ -195,6 +196,21 @@ __device__ __forceinline__ void d_window3_lean(const ResArgs& ra, int row, int y
     }
 }
 
+// Per-subband detector: whether X_f(y, x) of the newest frame (ring slot Tmod,
+// band f = row) is the maximum of its (2k+1)^2 window clipped to the image
+// (ties count).
+template <typename TS>
+__device__ __forceinline__ bool band_is_max(const ResArgs& ra, int row, int ys, int xs) {
+    const FilterArgs& a = ra.a;
+    const TS* plane = static_cast<const TS*>(ra.ring) + ((int64_t)ra.Tmod * ra.F + row) * a.P;
+    const float c = ld1(plane + (int64_t)ys * a.W + xs);
+    const int k = ra.band_k;
+    for (int yy = max(ys - k, 0); yy <= min(ys + k, a.H - 1); ++yy)
+        for (int xx = max(xs - k, 0); xx <= min(xs + k, a.W - 1); ++xx)
+            if (ld1(plane + (int64_t)yy * a.W + xx) > c) return false;
+    return true;
+}
+
 // Candidates of one image row of a warp (lanes with cand set): the 3x3 local
 // maximum of D clipped to the image (ties count); then one warp-aggregated
 // reservation and one record per DM trial of the delay row.  Every lane of the
@@ -204,7 +220,9 @@ __device__ __noinline__ void emit_res_candidates(const ResArgs& ra, int row, int
                                                  bool cand, int m0, int nm) {
     const FilterArgs& a = ra.a;
     const int lane = threadIdx.x & 31;
-    if (cand) {
+    if (cand && ra.band_k > 0) {
+        cand = band_is_max<TS>(ra, row, ys, xs);
+    } else if (cand) {
         float nb[9];
         d_window3_lean<TS>(ra, row, ys, xs, nb);
 #pragma unroll
@@ -503,8 +521,9 @@ __global__ void __launch_bounds__(FiltGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
 // k_lmax_res: the 3x3 local maximum of D (clipped to the image, ties count) at
 // every crossing of the list, one thread per crossing, D summed from the raw
 // ring on the window; one candidate record per DM trial of a maximum's delay
-// row (warp-aggregated reservations).
-template <typename TS>
+// row (warp-aggregated reservations).  BAND: the per-subband detector, the
+// (2k+1)^2 maximum of the band image X_row of the newest frame.
+template <typename TS, bool BAND>
 __global__ void __launch_bounds__(256) k_lmax_res(ResArgs ra) {
     const FilterArgs& a = ra.a;
     const unsigned long long nres = *ra.xcounter;
@@ -524,12 +543,16 @@ __global__ void __launch_bounds__(256) k_lmax_res(ResArgs ra) {
                 ys = (int)((key >> 16) & 0xffffu);
                 xs = (int)(key & 0xffffu);
                 snr = ra.xvals[i];
-                float nb[9];
-                d_window3<TS>(ra, row, ys, xs, nb);
-                cand = true;
+                if constexpr (BAND) {
+                    cand = band_is_max<TS>(ra, row, ys, xs);
+                } else {
+                    float nb[9];
+                    d_window3<TS>(ra, row, ys, xs, nb);
+                    cand = true;
 #pragma unroll
-                for (int k = 0; k < 9; ++k)
-                    if (k != 4 && nb[k] > nb[4]) cand = false;
+                    for (int k = 0; k < 9; ++k)
+                        if (k != 4 && nb[k] > nb[4]) cand = false;
+                }
             }
         }
         const int m0 = cand ? a.member_start[row] : 0;
@@ -566,6 +589,18 @@ constexpr size_t residual_smem_bytes() {
 template <int R>
 constexpr size_t res_filter_smem_bytes() {
     return ((size_t)2 * FiltGeom<R>::B * FiltGeom<R>::SD + (size_t)FiltGeom<R>::B * FiltGeom<R>::SX) * sizeof(float);
+}
+
+}  // namespace lpf
+
+namespace lpf {
+
+// Per-subband detector with a 16-bit ring: the residual planes X_f - C(X_f) of
+// the newest frame widened to FP32 (the images the filter reads).
+template <typename TS>
+__global__ void k_band_planes(const TS* __restrict__ res_slot, float* __restrict__ out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = ld1(res_slot + i);
 }
 
 }  // namespace lpf

@@ -291,6 +291,28 @@ void build_plan(lpf_stream* s) {
     }
 }
 
+// Per-subband detector: one row per band image of the newest frame (no delays),
+// "trial" f = band f.
+void build_band_plan(lpf_stream* s) {
+    const int F = s->F;
+    s->delay.assign((size_t)F * F, 0);
+    s->dmax.assign(F, 0);
+    s->max_delay = 0;
+    s->n_distinct = F;
+    s->ord2d.resize(F);
+    s->row_of_d.resize(F);
+    s->row_dmax.assign(F, 0);
+    s->member_start.resize(F + 1);
+    s->member_ord.resize(F);
+    for (int f = 0; f < F; ++f) {
+        s->ord2d[f] = f;
+        s->row_of_d[f] = f;
+        s->member_start[f] = f;
+        s->member_ord[f] = f;
+    }
+    s->member_start[F] = F;
+}
+
 int n_active_rows(const lpf_stream* s, int64_t T) {
     int64_t span = T - s->T_first;
     int n = 0;
@@ -342,6 +364,7 @@ lpf::ResArgs res_args(lpf_stream* s, const lpf::FilterArgs& a, int Tmod) {
     ra.xvals = s->xvals;
     ra.xcounter = reinterpret_cast<unsigned long long*>(s->d_counter + 2);
     ra.xcap = s->xcap;
+    ra.band_k = s->prm.mode == LPF_MODE_SUBBAND ? s->prm.lmax_r : 0;
     return ra;
 }
 
@@ -357,7 +380,10 @@ void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows, int 
 
 template <typename TS>
 void launch_lmax_res(lpf_stream* s, const lpf::FilterArgs& a, int Tmod) {
-    lpf::k_lmax_res<TS><<<148 * 8, 256, 0, s->st>>>(res_args(s, a, Tmod));
+    if (s->prm.mode == LPF_MODE_SUBBAND)
+        lpf::k_lmax_res<TS, true><<<148 * 8, 256, 0, s->st>>>(res_args(s, a, Tmod));
+    else
+        lpf::k_lmax_res<TS, false><<<148 * 8, 256, 0, s->st>>>(res_args(s, a, Tmod));
 }
 
 template <typename TS>
@@ -489,7 +515,21 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
     }
     lpf::k_zero_u32<<<1, 32, 0, s->st>>>(s->d_counter, 4);   // candidates, crossings (u64 at word 2)
     prof_mark(s, sl, ST_DEDISP);
-    if (n_rows > 0) {
+    // images the filter reads: D - C per distinct delay row, or (per-subband
+    // detector) the residual planes of the newest frame, in place for FP32
+    const float* filter_images = s->D;
+    if (s->prm.mode == LPF_MODE_SUBBAND) {
+        const int64_t n = (int64_t)s->F * s->P;
+        if (s->prm.dtype == LPF_FP32) {
+            filter_images = reinterpret_cast<const float*>(s->resring) + ring_slot * n;
+        } else if (s->prm.dtype == LPF_FP16) {
+            lpf::k_band_planes<__half><<<148 * 8, 256, 0, s->st>>>(
+                reinterpret_cast<const __half*>(s->resring) + ring_slot * n, s->D, n);
+        } else {
+            lpf::k_band_planes<__nv_bfloat16><<<148 * 8, 256, 0, s->st>>>(
+                reinterpret_cast<const __nv_bfloat16*>(s->resring) + ring_slot * n, s->D, n);
+        }
+    } else if (n_rows > 0) {
         switch (s->prm.dtype) {
             case LPF_FP32: launch_dedisperse<float>(s, n_rows, Tmod); break;
             case LPF_FP16: launch_dedisperse<__half>(s, n_rows, Tmod); break;
@@ -499,7 +539,7 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
     prof_mark(s, sl, ST_FILTER);
     lpf::FilterArgs a;
     if (n_rows > 0) {
-        a.D = s->D; a.P = s->P; a.H = s->H; a.W = s->W; a.r = s->prm.box_r; a.kappa = s->prm.kappa;
+        a.D = filter_images; a.P = s->P; a.H = s->H; a.W = s->W; a.r = s->prm.box_r; a.kappa = s->prm.kappa;
         a.tiles_x = s->tiles_x; a.tiles_y = s->tiles_y;
         a.member_start = s->d_member_start; a.member_ord = s->d_member_ord;
         a.keys = s->keys[0]; a.vals = s->vals[0]; a.counter = s->d_counter; a.cap = s->prm.cand_cap;
@@ -593,6 +633,7 @@ void lpf_default_params(lpf_params* p) {
     p->qc_z = 5.0f;
     p->qc_zeta = 20.0f;
     p->qc_min_frames = 128;
+    p->mode = LPF_MODE_DISPERSED;
 }
 
 const char* lpf_strerror(int code) {
@@ -626,10 +667,15 @@ int plan_stream(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, 
     lpf_params prm;
     lpf_default_params(&prm);
     if (params) prm = *params;
-    if (H <= 0 || W <= 0 || F <= 0 || n_dm <= 0 || !freqs_mhz || !dm_grid || buffer_depth <= 0)
-        return LPF_E_ARG;
+    if (prm.mode != LPF_MODE_DISPERSED && prm.mode != LPF_MODE_SUBBAND) return LPF_E_ARG;
+    const bool band = prm.mode == LPF_MODE_SUBBAND;
+    if (H <= 0 || W <= 0 || F <= 0 || !freqs_mhz || buffer_depth <= 0) return LPF_E_ARG;
+    if (!band && (n_dm <= 0 || !dm_grid)) return LPF_E_ARG;
     if (H > (1 << 16) || W > (1 << 16) || buffer_depth > 32767 || F > 32) return LPF_E_ARG;
-    if (!(prm.cadence_s > 0) || prm.box_r < 1 || prm.box_r > 16 || prm.lmax_r != 1) return LPF_E_ARG;
+    if (!(prm.cadence_s > 0) || prm.box_r < 1 || prm.box_r > 16) return LPF_E_ARG;
+    if (band ? (prm.lmax_r < 1 || prm.lmax_r > 3) : prm.lmax_r != 1) return LPF_E_ARG;
+    // the per-subband detector runs on the residual planes: streaming filter only
+    if (band && (prm.filter_impl == 1 || (prm.box_r != 7 && prm.box_r != 15))) return LPF_E_ARG;
     if (prm.dtype < LPF_FP32 || prm.dtype > LPF_BF16 || prm.cand_cap < 1 || prm.dyn_box_r < 0) return LPF_E_ARG;
     if (prm.result_slots < 1 || prm.result_slots > kMaxSlots) return LPF_E_ARG;
     if (!std::isfinite(prm.kappa)) return LPF_E_ARG;
@@ -641,25 +687,29 @@ int plan_stream(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, 
         return LPF_E_ARG;
     for (int f = 0; f < F; ++f)
         if (!(freqs_mhz[f] > 0) || !std::isfinite(freqs_mhz[f])) return LPF_E_ARG;
-    for (int d = 0; d < n_dm; ++d)
+    for (int d = 0; !band && d < n_dm; ++d)
         if (!(dm_grid[d] >= 0) || !std::isfinite(dm_grid[d])) return LPF_E_ARG;
 
     lpf_stream* s = new (std::nothrow) lpf_stream();
     if (!s) return LPF_E_OOM;
-    s->H = H; s->W = W; s->F = F; s->n_dm = n_dm; s->depth = buffer_depth; s->prm = prm;
+    s->H = H; s->W = W; s->F = F; s->n_dm = band ? F : n_dm; s->depth = buffer_depth; s->prm = prm;
     s->HW = (int64_t)H * W;
     s->P = (s->HW + 7) / 8 * 8;
     s->elem = prm.dtype == LPF_FP32 ? 4 : 2;
     s->n_slots = prm.result_slots;
-    build_delay_table(s, freqs_mhz, dm_grid);
-    if (buffer_depth < s->max_delay + 1) {
-        delete s;
-        return LPF_E_DEPTH;
+    if (band) {
+        build_band_plan(s);
+    } else {
+        build_delay_table(s, freqs_mhz, dm_grid);
+        if (buffer_depth < s->max_delay + 1) {
+            delete s;
+            return LPF_E_DEPTH;
+        }
+        build_plan(s);
     }
-    build_plan(s);
     s->bx = std::max(1, ceil_log2(W));
     s->by = std::max(1, ceil_log2(H));
-    s->bo = std::max(1, ceil_log2(n_dm));
+    s->bo = std::max(1, ceil_log2(s->n_dm));
     s->key_bits = s->bx + s->by + s->bo;
     if (s->key_bits > 64) {
         delete s;
@@ -669,7 +719,7 @@ int plan_stream(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, 
     s->tiles_y = (H + lpf::kTile - 1) / lpf::kTile;
     s->filter_rmax = prm.box_r <= 8 ? 8 : 16;
     s->filter_smem = filter_smem_bytes(prm.box_r, s->filter_rmax);
-    s->stream_filter = prm.filter_impl == 2 || (prm.filter_impl == 0 && (prm.box_r == 7 || prm.box_r == 15));
+    s->stream_filter = band || prm.filter_impl == 2 || (prm.filter_impl == 0 && (prm.box_r == 7 || prm.box_r == 15));
     s->n_strips = (W + lpf::kStreamTX - 1) / lpf::kStreamTX;
     // crossing list of the residual path: room for 1/32 of all pixels of all
     // delay rows above the threshold (a swamped frame overflows into the slower
@@ -769,8 +819,8 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_chg, (size_t)s->n_distinct);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_member_start, s->member_start.size());
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_member_ord, s->member_ord.size());
-    if (rc == LPF_OK) rc = dev_alloc(s, &s->d_ord2d, (size_t)n_dm);
-    if (rc == LPF_OK) rc = dev_alloc(s, &s->d_dmax, (size_t)n_dm);
+    if (rc == LPF_OK) rc = dev_alloc(s, &s->d_ord2d, (size_t)s->n_dm);
+    if (rc == LPF_OK) rc = dev_alloc(s, &s->d_dmax, (size_t)s->n_dm);
     for (int i = 0; i < 2 && rc == LPF_OK; ++i) {
         rc = dev_alloc(s, &s->keys[i], (size_t)prm.cand_cap);
         if (rc == LPF_OK) rc = dev_alloc(s, &s->vals[i], (size_t)prm.cand_cap);
@@ -838,7 +888,7 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
         delete s;
         return rc;
     }
-    s->last_stats.assign((size_t)n_dm * 2, std::nan(""));
+    s->last_stats.assign((size_t)s->n_dm * 2, std::nan(""));
     *out = s;
     return LPF_OK;
 }

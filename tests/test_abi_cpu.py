@@ -37,7 +37,7 @@ def test_struct_layouts():
     assert (p.cadence_s, p.kappa, p.box_r, p.lmax_r, p.dtype) == (1.0, 6.0, 15, 1, 0)
     assert p.cand_cap == 1 << 20 and p.result_slots == 2 and not p.cuda_stream
     # the fields after the pointer read back the library's defaults: same layout
-    assert (p.filter_impl, p.qc, p.qc_z, p.qc_zeta, p.qc_min_frames) == (0, 0, 5.0, 20.0, 128)
+    assert (p.filter_impl, p.qc, p.qc_z, p.qc_zeta, p.qc_min_frames, p.mode) == (0, 0, 5.0, 20.0, 128, 0)
 
 
 def test_strerror_names_every_code():
@@ -61,6 +61,10 @@ def test_argument_validation_before_any_cuda_call():
         dict(H=8, W=8, freqs_mhz=f, dm_grid=dm, depth=8, qc=True, qc_z=0.0),
         dict(H=8, W=8, freqs_mhz=f, dm_grid=dm, depth=8, qc=True, qc_zeta=-1.0),
         dict(H=8, W=8, freqs_mhz=f, dm_grid=dm, depth=8, qc=True, qc_min_frames=1),
+        dict(H=8, W=8, freqs_mhz=f, dm_grid=dm, depth=8, lmax_r=3),              # 3x3 only for DM trials
+        dict(H=8, W=8, freqs_mhz=f, dm_grid=None, depth=2, mode="subband", lmax_r=4),
+        dict(H=8, W=8, freqs_mhz=f, dm_grid=None, depth=2, mode="subband", box_r=5),
+        dict(H=8, W=8, freqs_mhz=f, dm_grid=None, depth=2, mode="subband", filter_impl="tiled"),
     ]
     for kw in bad:
         with pytest.raises(lpf.LpfError) as e:
@@ -123,3 +127,15 @@ def test_quality_control_footprint():
     on = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth, qc=True)
     planes = 2 * sp.F * sp.H * sp.W * 4
     assert planes < on - off < planes + 64 * 1024
+
+
+def test_subband_detector_footprint():
+    """Per-subband detector: F rows of images (one per band), no delay table, any
+    depth >= 1, dm_grid not needed."""
+    import synth
+    sp = synth.spec_aartfaac(H=256, W=256)
+    fp = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, None, 2, mode="subband", lmax_r=3)
+    rings = 2 * 2 * sp.F * sp.H * sp.W * 4          # raw and residual rings, depth 2
+    imgs = sp.F * sp.H * sp.W * 4
+    # plus the 1M-record candidate, crossing and result buffers and two staging frames
+    assert rings + imgs < fp < rings + imgs + 128 * 2 ** 20
