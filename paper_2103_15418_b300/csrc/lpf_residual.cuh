@@ -392,10 +392,20 @@ __global__ void __launch_bounds__(FiltGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
             }
         }
     };
+    // row segment blockIdx.z: blocks [k0, k1); a segment after the first starts one
+    // block early, to build the suffix sums of the vertical two-stack (no output)
     const int nblk = (H + R + B - 1) / B;
-    load(0, 0, NT);
+    const int seg_blocks = (nblk + (int)gridDim.z - 1) / (int)gridDim.z;
+    const int k0 = (int)blockIdx.z * seg_blocks, k1 = min(nblk, k0 + seg_blocks);
+    double* partial = a.partials + (((int64_t)row * gridDim.z + blockIdx.z) * gridDim.x + strip) * 3;
+    if (k0 >= k1) {
+        if (t == 0) { partial[0] = 0.0; partial[1] = 0.0; partial[2] = 0.0; }
+        return;
+    }
+    const int kbeg = k0 > 0 ? k0 - 1 : 0;
+    load(kbeg, 0, NT);
     cp_async_commit();
-    for (int k = 0; k < nblk; ++k) {
+    for (int k = kbeg; k < k1; ++k) {
         const int ybase = k * B;
         const float* cur = Rb + (k & 1) * B * SD;
         // one barrier both publishes the copies of block k and ends the vertical
@@ -413,8 +423,13 @@ __global__ void __launch_bounds__(FiltGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
         __syncthreads();
         if (loader) {
             // ---- the next block's copies while the column warps run the vertical pass
-            if (k + 1 < nblk) load(k + 1, TX, NT - TX);
+            if (k + 1 < k1) load(k + 1, TX, NT - TX);
             cp_async_commit();
+        } else if (k < k0) {
+            // warm-up block: the suffix sums of its last (2r+1)-row segment
+            float acc = 0.f;
+#pragma unroll
+            for (int i = L - 1; i >= 1; --i) { acc += hE[((NP - 1) * L + i) * SX + t]; suf[i] = acc; }
         } else {
             // R(ys) of the rows of block k-1 (ys = ybase - r .. ybase - 1), from
             // global memory, loaded ahead of the pass
@@ -513,8 +528,7 @@ __global__ void __launch_bounds__(FiltGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
     if (t == 0) {
         double q1 = 0, q2 = 0, qc = 0;
         for (int w = 0; w < NT / 32; ++w) { q1 += red[w][0]; q2 += red[w][1]; qc += red[w][2]; }
-        double* p = a.partials + ((int64_t)row * gridDim.x + strip) * 3;
-        p[0] = q1; p[1] = q2; p[2] = qc;
+        partial[0] = q1; partial[1] = q2; partial[2] = qc;
     }
 }
 

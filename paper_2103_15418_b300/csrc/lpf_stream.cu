@@ -128,7 +128,8 @@ struct lpf_stream {
     int tiles_x = 0, tiles_y = 0;
     size_t filter_smem = 0;
     int filter_rmax = 16;
-    bool stream_filter = false;     // residual path: k_residual + k_filter_res (box_r 7 or 15)
+    bool stream_filter = false;
+    int fseg = 1;                   // row segments per strip of the streaming filter     // residual path: k_residual + k_filter_res (box_r 7 or 15)
     void* resring = nullptr;        // [depth][F][P] per-subband residual X - C(X), storage type
     int n_strips = 0;
 
@@ -371,7 +372,7 @@ lpf::ResArgs res_args(lpf_stream* s, const lpf::FilterArgs& a, int Tmod) {
 template <typename TS>
 void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows, int Tmod) {
     const lpf::ResArgs ra = res_args(s, a, Tmod);
-    dim3 grid((unsigned)s->n_strips, (unsigned)n_rows);
+    dim3 grid((unsigned)s->n_strips, (unsigned)n_rows, (unsigned)s->fseg);
     if (s->prm.box_r == 7)
         lpf::k_filter_res<7, TS><<<grid, lpf::FiltGeom<7>::NT, lpf::res_filter_smem_bytes<7>(), s->st>>>(ra);
     else
@@ -455,7 +456,7 @@ void launch_dynspec(lpf_stream* s, int n, int Tw, int slot_first, float* out) {
 }
 
 int n_filter_blocks(const lpf_stream* s) {
-    return s->stream_filter ? s->n_strips : s->tiles_x * s->tiles_y;
+    return s->stream_filter ? s->n_strips * s->fseg : s->tiles_x * s->tiles_y;
 }
 
 size_t filter_smem_bytes(int r, int rmax) {
@@ -721,6 +722,15 @@ int plan_stream(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, 
     s->filter_smem = filter_smem_bytes(prm.box_r, s->filter_rmax);
     s->stream_filter = band || prm.filter_impl == 2 || (prm.filter_impl == 0 && (prm.box_r == 7 || prm.box_r == 15));
     s->n_strips = (W + lpf::kStreamTX - 1) / lpf::kStreamTX;
+    // the per-subband detector has only F rows: split each strip into row segments
+    // so that about two waves of 4 CTAs per SM run (each segment after the first
+    // re-reads one block of rows); the dispersed search has enough rows
+    if (band) {
+        const int B = prm.box_r == 7 ? lpf::FiltGeom<7>::B : lpf::FiltGeom<15>::B;
+        const int nblk = (H + prm.box_r + B - 1) / B;
+        const int want = (2 * 4 * 148 + s->n_strips * F - 1) / (s->n_strips * F);
+        s->fseg = std::max(1, std::min(want, nblk / 2));
+    }
     // crossing list of the residual path: room for 1/32 of all pixels of all
     // delay rows above the threshold (a swamped frame overflows into the slower
     // in-kernel resolution, with the same results)
