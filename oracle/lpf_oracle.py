@@ -21,6 +21,8 @@ method, each citing the passage of Ruhe et al. (arXiv 2103.15418) it follows:
                    residuals X - C(X) (linearity of the local centre); reference
                    for rings that store those residuals in reduced precision
   subband_detect   Sec. 2.1.1-2.1.2 on every band image, (2k+1)^2 maximum (k = 3)
+  clip_detect      Sec. 2.1.1 iterated: C and S re-estimated from the pixels not
+                   yet flagged, until no new flag or the iteration limit
   qc_band_scores   App. A, z = (b - median(b)) / MAD(b) of the band-image means
   QCState, qc_frame  App. A, per-pixel running mean / standard deviation
                    (Welford) and scores zeta; bands over either threshold are
@@ -395,3 +397,34 @@ def subband_detect(frame: np.ndarray, r: int, kappa: float, k: int = 3):
         maps[b] = res
     cands.sort(key=lambda c: (c[0], c[1], c[2]))
     return cands, stats, maps
+
+
+def clip_detect(D: np.ndarray, r: int, kappa: float, k: int = 1, iters: int = 1) -> Dict[str, np.ndarray]:
+    """Iterated sigma clipping of one image (Sec. 2.1.1): at each iteration C and S
+    are the box means over the window pixels not yet flagged (the count of those
+    pixels normalises), y = I(snr > kappa) is added to the flags, and the loop
+    stops when an iteration flags no new pixel or after iters iterations.  The
+    peaks are the (2k+1)^2 maxima of D among the flagged pixels (Sec. 2.1.2); the
+    S/N is that of the last iteration.  iters = 1 is detect().
+    """
+    D = np.asarray(D, np.float64)
+    flags = np.zeros(D.shape, bool)
+    C = S = snr = None
+    n = None
+    for _ in range(max(int(iters), 1)):
+        m = (~flags).astype(np.float64)
+        n = box_sum(m, r)
+        ok = n > 0
+        C = np.zeros_like(D)
+        C[ok] = box_sum(D * m, r)[ok] / n[ok]
+        S = np.zeros_like(D)
+        S[ok] = box_sum((D - C) ** 2 * m, r)[ok] / n[ok]
+        snr = snr_map(D, C, S)
+        above = snr > kappa
+        new = above & ~flags
+        flags |= above
+        if not new.any():
+            break
+    q = local_max_mask(D, k)
+    return dict(C=C, S=S, snr=snr, valid=S > 0, flags=flags, mask=flags & q & (S > 0),
+                lmax_margin=D - neighbour_max(D, k))

@@ -556,3 +556,56 @@ def test_subband_detect_is_detect_per_band():
         assert np.array_equal(maps[b]["mask"], ref["mask"])
         got = sorted((y, xq) for bb, y, xq, _ in cands if bb == b)
         assert got == sorted(zip(*np.nonzero(ref["mask"])))
+
+
+# ----------------------------------------------------------------- iterated sigma clipping (Sec. 2.1.1)
+def test_clip_one_iteration_is_the_one_pass_filter():
+    rng = np.random.default_rng(19)
+    D = rng.standard_normal((30, 34))
+    D[10, 12] += 25.0
+    a = O.clip_detect(D, 5, 4.0, k=1, iters=1)
+    b = O.detect(D, 5, 4.0, 1)
+    assert np.array_equal(a["mask"], b["mask"]) and np.allclose(a["snr"], b["snr"], atol=1e-12)
+
+
+def test_clip_masked_means_by_brute_force():
+    """Second iteration: C and S at every pixel from the unflagged window pixels only."""
+    rng = np.random.default_rng(20)
+    D = rng.standard_normal((14, 15))
+    D[6, 7] += 40.0
+    r = 2                                    # a lone delta reaches sqrt(24) = 4.9 in a 5x5 window
+    first = O.clip_detect(D, r, 4.0, iters=1)
+    flags = first["snr"] > 4.0
+    assert flags[6, 7] and flags.sum() == 1
+    second = O.clip_detect(D, r, 4.0, iters=2)
+    H, W = D.shape
+    for y in range(H):
+        for x in range(W):
+            vals = [D[yy, xx] for yy in range(max(0, y - r), min(H, y + r + 1))
+                    for xx in range(max(0, x - r), min(W, x + r + 1)) if not flags[yy, xx]]
+            c = sum(vals) / len(vals)
+            assert abs(second["C"][y, x] - c) < 1e-12
+    # S uses C at each window pixel (two-pass), over the same pixels
+    y, x = 6, 7
+    terms = [(D[yy, xx] - second["C"][yy, xx]) ** 2 for yy in range(y - r, y + r + 1)
+             for xx in range(x - r, x + r + 1) if not flags[yy, xx]]
+    assert abs(second["S"][y, x] - sum(terms) / len(terms)) < 1e-12
+
+
+def test_clip_unmasks_a_faint_source_beside_a_bright_one():
+    """One pass: a bright point source inflates the spread around it and hides a
+    faint source 6 px away; once the bright pixel is flagged (first pass) and left
+    out of C and S (second pass) the faint one crosses the threshold; a third pass
+    flags nothing new and the loop stops."""
+    rng = np.random.default_rng(22)
+    D = rng.standard_normal((64, 64))
+    yy, xx = np.mgrid[:64, :64]
+    D[30, 30] += 400.0
+    D += 9.0 * np.exp(-((yy - 30) ** 2 + (xx - 36) ** 2) / (2 * 1.0 ** 2))
+    one = O.clip_detect(D, 7, 6.0, k=1, iters=1)
+    many = O.clip_detect(D, 7, 6.0, k=1, iters=6)
+    assert not one["mask"][30, 36] and many["mask"][30, 36]
+    assert many["mask"][30, 30]
+    # the loop stops once nothing new is flagged: more iterations change nothing
+    more = O.clip_detect(D, 7, 6.0, k=1, iters=12)
+    assert np.array_equal(more["mask"], many["mask"]) and np.array_equal(more["flags"], many["flags"])
