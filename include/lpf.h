@@ -95,6 +95,13 @@ typedef struct {
      * lpf_stream_open are then ignored (0 and NULL allowed); a candidate's dm_idx
      * is its band f and t0 its frame T; lpf_get_stats has one row per band.     */
     int    mode;          /* LPF_MODE_DISPERSED / LPF_MODE_SUBBAND                 default DISPERSED */
+    /* Per-subband detector only: iterated sigma clipping (Sec. 2.1.1).  Each
+     * iteration re-estimates C and S from the window pixels not yet flagged and
+     * adds the pixels over the threshold to the flags, until an iteration flags
+     * nothing new or clip_iters iterations; candidates are the flagged (2 lmax_r
+     * + 1)^2 maxima of X_f, with the S/N of the last iteration.  1 = one pass
+     * (the residual filter).                                                    */
+    int    clip_iters;    /* 1..16 (> 1 only with LPF_MODE_SUBBAND)                default 1 */
 } lpf_params;
 
 /* One candidate: pixel (y, x) of DM trial dm_idx (index into dm_grid) whose

@@ -11,6 +11,7 @@
 #include "lpf_dedisperse.cuh"
 #include "lpf_residual.cuh"
 #include "lpf_qc.cuh"
+#include "lpf_clip.cuh"
 
 #include <algorithm>
 #include <chrono>
@@ -107,6 +108,10 @@ struct lpf_stream {
     unsigned* qc_words = nullptr;    // [2] pixel flags, discard mask
     lpf::QcRecord* h_qc = nullptr;   // [slots] pinned
     lpf::QcRecord last_qc{};
+    // iterated clipping of the per-subband detector (clip_iters > 1)
+    uint8_t* clip_flags = nullptr;   // [F][P]
+    float* clip_planes = nullptr;    // T1, T2, C, N, S: 5 x [F][P]
+    unsigned* clip_changed = nullptr;  // [clip_iters]
     int64_t last_qc_T = -1;
     double* h_stats = nullptr;       // [slots][n_distinct][3]
 
@@ -183,6 +188,9 @@ void free_all(lpf_stream* s) {
             if (e) cudaEventDestroy(e);
     if (s->h_count) cudaFreeHost(s->h_count);
     if (s->h_qc) cudaFreeHost(s->h_qc);
+    if (s->clip_flags) cudaFree(s->clip_flags);
+    if (s->clip_planes) cudaFree(s->clip_planes);
+    if (s->clip_changed) cudaFree(s->clip_changed);
     {
         void* q[] = {s->qc_mean, s->qc_m2, s->qc_n, s->qc_invn, s->qc_part, s->qc_words};
         for (void* p : q)
@@ -507,7 +515,8 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
         case LPF_FP16: launch_ingest<__half>(s, frame_dev, ring_slot); break;
         default: launch_ingest<__nv_bfloat16>(s, frame_dev, ring_slot); break;
     }
-    if (s->stream_filter) {
+    const bool clip = s->prm.clip_iters > 1;
+    if (s->stream_filter && !clip) {
         switch (s->prm.dtype) {
             case LPF_FP32: launch_residual<float>(s, ring_slot); break;
             case LPF_FP16: launch_residual<__half>(s, ring_slot); break;
@@ -519,7 +528,40 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
     // images the filter reads: D - C per distinct delay row, or (per-subband
     // detector) the residual planes of the newest frame, in place for FP32
     const float* filter_images = s->D;
-    if (s->prm.mode == LPF_MODE_SUBBAND) {
+    lpf::ClipArgs ca{};
+    if (clip) {
+        const int64_t n = (int64_t)s->F * s->P;
+        ca.X = s->D;
+        ca.flags = s->clip_flags;
+        ca.T1 = s->clip_planes;
+        ca.T2 = ca.T1 + n;
+        ca.C = ca.T2 + n;
+        ca.N = ca.C + n;
+        ca.S = ca.N + n;
+        ca.changed = s->clip_changed;
+        ca.F = s->F; ca.H = s->H; ca.W = s->W; ca.r = s->prm.box_r; ca.P = s->P; ca.kappa = s->prm.kappa;
+        const int g = 148 * 8;
+        lpf::k_zero_u32<<<1, 32, 0, s->st>>>(s->clip_changed, s->prm.clip_iters);
+        switch (s->prm.dtype) {
+            case LPF_FP32:
+                lpf::k_clip_init<float><<<g, 256, 0, s->st>>>(ca, reinterpret_cast<const float*>(s->ring) + ring_slot * n);
+                break;
+            case LPF_FP16:
+                lpf::k_clip_init<__half><<<g, 256, 0, s->st>>>(ca, reinterpret_cast<const __half*>(s->ring) + ring_slot * n);
+                break;
+            default:
+                lpf::k_clip_init<__nv_bfloat16><<<g, 256, 0, s->st>>>(
+                    ca, reinterpret_cast<const __nv_bfloat16*>(s->ring) + ring_slot * n);
+                break;
+        }
+        for (int it = 0; it < s->prm.clip_iters; ++it) {
+            lpf::k_clip_rows<0><<<g, 256, 0, s->st>>>(ca, it);
+            lpf::k_clip_cols<0><<<g, 256, 0, s->st>>>(ca, it);
+            lpf::k_clip_rows<1><<<g, 256, 0, s->st>>>(ca, it);
+            lpf::k_clip_cols<1><<<g, 256, 0, s->st>>>(ca, it);
+            lpf::k_clip_flag<<<g, 256, 0, s->st>>>(ca, it);
+        }
+    } else if (s->prm.mode == LPF_MODE_SUBBAND) {
         const int64_t n = (int64_t)s->F * s->P;
         if (s->prm.dtype == LPF_FP32) {
             filter_images = reinterpret_cast<const float*>(s->resring) + ring_slot * n;
@@ -545,7 +587,10 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
         a.member_start = s->d_member_start; a.member_ord = s->d_member_ord;
         a.keys = s->keys[0]; a.vals = s->vals[0]; a.counter = s->d_counter; a.cap = s->prm.cand_cap;
         a.bx = s->bx; a.by = s->by; a.partials = s->d_partials;
-        if (s->stream_filter) {
+        if (clip) {
+            lpf::k_clip_emit<<<dim3((unsigned)n_filter_blocks(s), (unsigned)s->F), 256, 0, s->st>>>(
+                ca, a, s->prm.lmax_r);
+        } else if (s->stream_filter) {
             switch (s->prm.dtype) {
                 case LPF_FP32: launch_filter_res<float>(s, a, n_rows, Tmod); break;
                 case LPF_FP16: launch_filter_res<__half>(s, a, n_rows, Tmod); break;
@@ -560,7 +605,7 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
         }
     }
     prof_mark(s, sl, ST_LMAX);
-    if (n_rows > 0 && s->stream_filter) {
+    if (n_rows > 0 && s->stream_filter && !clip) {
         switch (s->prm.dtype) {
             case LPF_FP32: launch_lmax_res<float>(s, a, Tmod); break;
             case LPF_FP16: launch_lmax_res<__half>(s, a, Tmod); break;
@@ -635,6 +680,7 @@ void lpf_default_params(lpf_params* p) {
     p->qc_zeta = 20.0f;
     p->qc_min_frames = 128;
     p->mode = LPF_MODE_DISPERSED;
+    p->clip_iters = 1;
 }
 
 const char* lpf_strerror(int code) {
@@ -677,6 +723,8 @@ int plan_stream(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, 
     if (band ? (prm.lmax_r < 1 || prm.lmax_r > 3) : prm.lmax_r != 1) return LPF_E_ARG;
     // the per-subband detector runs on the residual planes: streaming filter only
     if (band && (prm.filter_impl == 1 || (prm.box_r != 7 && prm.box_r != 15))) return LPF_E_ARG;
+    // iterated clipping: per-subband detector only (the dispersed search is one pass)
+    if (prm.clip_iters < 1 || prm.clip_iters > 16 || (!band && prm.clip_iters != 1)) return LPF_E_ARG;
     if (prm.dtype < LPF_FP32 || prm.dtype > LPF_BF16 || prm.cand_cap < 1 || prm.dyn_box_r < 0) return LPF_E_ARG;
     if (prm.result_slots < 1 || prm.result_slots > kMaxSlots) return LPF_E_ARG;
     if (!std::isfinite(prm.kappa)) return LPF_E_ARG;
@@ -749,6 +797,8 @@ size_t footprint_bytes(const lpf_stream* s) {
     size_t t = (size_t)s->depth * s->F * s->P * s->elem * (s->stream_filter ? 2 : 1);
     t += b(nd * s->P * 4) + b(2 * (size_t)s->F * s->HW * 4) + b(nd * s->F * 2) + b(nd * 4);
     if (s->xcap > 0) t += b((size_t)s->xcap * 8) + b((size_t)s->xcap * 4);
+    if (s->prm.clip_iters > 1)
+        t += b((size_t)s->F * s->P) + b(5 * (size_t)s->F * s->P * 4) + b((size_t)s->prm.clip_iters * 4);
     if (s->prm.qc) {
         t += 2 * b((size_t)s->F * s->P * 4) + b((size_t)s->F * 4) + b((size_t)s->F * 4) +
              b((size_t)s->F * lpf::kQcScanBlocks * 8) + b(2 * 4);
@@ -843,6 +893,11 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
         if (rc == LPF_OK) rc = dev_alloc(s, &s->slots[i].d_stats, (size_t)s->n_distinct * 3);
         if (rc == LPF_OK && cudaEventCreateWithFlags(&s->slots[i].done, cudaEventDisableTiming) != cudaSuccess)
             rc = LPF_E_CUDA;
+    }
+    if (prm.clip_iters > 1) {
+        if (rc == LPF_OK) rc = dev_alloc(s, &s->clip_flags, (size_t)F * s->P);
+        if (rc == LPF_OK) rc = dev_alloc(s, &s->clip_planes, 5 * (size_t)F * s->P);
+        if (rc == LPF_OK) rc = dev_alloc(s, &s->clip_changed, (size_t)prm.clip_iters);
     }
     if (prm.qc) {
         if (rc == LPF_OK) rc = dev_alloc(s, &s->qc_mean, (size_t)F * s->P);

@@ -37,7 +37,8 @@ def test_struct_layouts():
     assert (p.cadence_s, p.kappa, p.box_r, p.lmax_r, p.dtype) == (1.0, 6.0, 15, 1, 0)
     assert p.cand_cap == 1 << 20 and p.result_slots == 2 and not p.cuda_stream
     # the fields after the pointer read back the library's defaults: same layout
-    assert (p.filter_impl, p.qc, p.qc_z, p.qc_zeta, p.qc_min_frames, p.mode) == (0, 0, 5.0, 20.0, 128, 0)
+    assert (p.filter_impl, p.qc, p.qc_z, p.qc_zeta, p.qc_min_frames, p.mode, p.clip_iters) == \
+        (0, 0, 5.0, 20.0, 128, 0, 1)
 
 
 def test_strerror_names_every_code():
@@ -65,6 +66,8 @@ def test_argument_validation_before_any_cuda_call():
         dict(H=8, W=8, freqs_mhz=f, dm_grid=None, depth=2, mode="subband", lmax_r=4),
         dict(H=8, W=8, freqs_mhz=f, dm_grid=None, depth=2, mode="subband", box_r=5),
         dict(H=8, W=8, freqs_mhz=f, dm_grid=None, depth=2, mode="subband", filter_impl="tiled"),
+        dict(H=8, W=8, freqs_mhz=f, dm_grid=dm, depth=8, clip_iters=3),        # one pass for DM trials
+        dict(H=8, W=8, freqs_mhz=f, dm_grid=None, depth=2, mode="subband", clip_iters=17),
     ]
     for kw in bad:
         with pytest.raises(lpf.LpfError) as e:
@@ -139,3 +142,13 @@ def test_subband_detector_footprint():
     imgs = sp.F * sp.H * sp.W * 4
     # plus the 1M-record candidate, crossing and result buffers and two staging frames
     assert rings + imgs < fp < rings + imgs + 128 * 2 ** 20
+
+
+def test_clipping_footprint():
+    """Iterated clipping adds a flag plane and five FP32 planes per band."""
+    import synth
+    sp = synth.spec_aartfaac(H=256, W=256)
+    one = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, None, 2, mode="subband", lmax_r=3)
+    many = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, None, 2, mode="subband", lmax_r=3, clip_iters=4)
+    px = sp.F * sp.H * sp.W
+    assert px * 21 <= many - one < px * 21 + 4096

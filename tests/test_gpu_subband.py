@@ -81,3 +81,45 @@ def test_subband_detector_7x7_deblends(lib):
     for (y0, x0) in pairs:
         assert (0, y0, x0) in got[3] and (0, y0, x0) in got[1]
         assert (0, y0, x0 + 3) in got[1] and (0, y0, x0 + 3) not in got[3]
+
+
+def clip_frame(spec, st, T):
+    """The noise-and-gradient stream with planted bright point sources, each with a
+    faint compact source 5 px away that the one-pass filter misses (band-dependent
+    positions)."""
+    x = st.frame(T)
+    yy, xx = np.mgrid[:spec.H, :spec.W]
+    for b in range(spec.F):
+        for j, (y0, x0) in enumerate([(20, 24), (60, 90), (30, 100), (80, 40)]):
+            y0 = (y0 + 3 * b + 7 * T) % (spec.H - 20) + 10
+            x0 = (x0 + 5 * b + 11 * T) % (spec.W - 30) + 10
+            x[b, y0, x0] += 300.0
+            x[b] += 10.0 * np.exp(-((yy - y0) ** 2 + (xx - x0 - 5) ** 2) / 2.0)
+    return x.astype(np.float32)
+
+
+@pytest.mark.parametrize("dtype", ["fp32", "fp16"])
+def test_subband_clipping_matches_oracle(lib, dtype):
+    spec = synth.spec_aartfaac(H=96, W=128, n_sources=0, n_pulses=0, box_r=7, n_frames=6)
+    st = synth.SyntheticStream(spec, seed=31)
+    k, iters, more = 3, 4, 0
+    with lib.Stream(spec.H, spec.W, spec.freqs_mhz, None, 1, kappa=spec.kappa, box_r=spec.box_r, dtype=dtype,
+                    mode="subband", lmax_r=k, clip_iters=iters) as s:
+        for T in range(3):
+            frame = clip_frame(spec, st, T)
+            s.push(torch.from_numpy(frame).cuda(), T)
+            _, c, n, trunc = s.poll(timeout_ms=60000)
+            assert not trunc and n == len(c) and np.all(c["t0"] == T)
+            assert_sorted_unique(c)
+            x = O.storage_round(frame, dtype)
+            gstats = s.stats()
+            for b in range(spec.F):
+                m = O.clip_detect(x[b], spec.box_r, spec.kappa, k, iters)
+                m["abs_sum"] = np.abs(x[b])
+                compare_trial(c[c["dm_idx"] == b], m, 1, spec.kappa)
+                one = O.clip_detect(x[b], spec.box_r, spec.kappa, k, 1)
+                more += int(m["mask"].sum() - one["mask"].sum())
+                mean, rms, _ = O.frame_stats(m["snr"], m["valid"])
+                assert abs(gstats[b][0] - mean) <= 1e-4 * abs(mean) + 1e-6, (b, gstats[b], mean)
+                assert abs(gstats[b][1] - rms) <= 1e-4 * abs(rms) + 1e-6, (b, gstats[b], rms)
+    assert more > 0          # clipping found sources the one-pass filter missed
