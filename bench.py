@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pool", type=int, default=12, help="distinct synthetic frames cycled")
+    ap.add_argument("--clip-iters", type=int, default=1,
+                    help="subband workload: sigma-clip iterations (1 = one pass)")
     ap.add_argument("--qc", action="store_true",
                     help="quality control of every frame before the search (band and pixel scores)")
     ap.add_argument("--workload", default="aartfaac", choices=["aartfaac", "serving", "subband"],
@@ -415,7 +417,8 @@ def run_subband(args):
     pool = [torch.from_numpy(st.frame(t)).cuda() for t in range(args.pool)]
     cur = torch.cuda.current_stream()
     s = lpf.Stream(spec.H, spec.W, spec.freqs_mhz, None, 2, kappa=spec.kappa, box_r=spec.box_r,
-                   dtype=args.dtype, result_slots=RESULT_SLOTS, cuda_stream=cur, mode="subband", lmax_r=3)
+                   dtype=args.dtype, result_slots=RESULT_SLOTS, cuda_stream=cur, mode="subband", lmax_r=3,
+                   clip_iters=args.clip_iters)
     T = 0
     for _ in range(args.warmup + 2):
         s.push(pool[T % args.pool], T)
@@ -444,6 +447,7 @@ def run_subband(args):
     print(json.dumps({
         "metric": "pixel*bands/s", "value": px * args.steps / elapsed, "unit": "pixel*bands/s",
         "workload": "subband-detector-1024x1024-16bands-box31-max7x7", "storage": args.dtype,
+        "clip_iters": args.clip_iters,
         "steps": args.steps, "ms_per_step": 1e3 * elapsed / args.steps,
         "kernel_ms_per_step": per_push, "candidates_per_step": float(np.mean(ncand)),
         "data": "synthetic (seeded AARTFAAC-shaped stream)"}), flush=True)
