@@ -40,6 +40,19 @@ int ceil_log2(int64_t v) {
     return b;
 }
 
+// Candidate buffers of one push.  Consecutive pushes alternate between two
+// lanes, so that the ordering, formatting and statistics of push T (its tail,
+// on a second stream) overlap the ingest and search of push T + 1.
+struct PushLane {
+    uint64_t* keys[2] = {nullptr, nullptr};
+    float* vals[2] = {nullptr, nullptr};
+    unsigned* counter = nullptr;       // [4]: candidates, -, crossings (u64 at word 2)
+    unsigned* hist = nullptr;          // radix-sort block histograms
+    double* partials = nullptr;        // [n_distinct][filter blocks][3]
+    cudaEvent_t lmax_done = nullptr;   // the push's 3x3 pass finished: its tail may start
+    cudaEvent_t tail_done = nullptr;   // the push's tail finished: the lane may be reused
+};
+
 struct Slot {
     int64_t T = -1;
     int n_active = 0;
@@ -87,11 +100,9 @@ struct lpf_stream {
     int* d_member_ord = nullptr;
     int* d_ord2d = nullptr;
     int* d_dmax = nullptr;
-    uint64_t* keys[2] = {nullptr, nullptr};
-    float* vals[2] = {nullptr, nullptr};
-    unsigned* d_counter = nullptr;
-    unsigned* d_hist = nullptr;
-    double* d_partials = nullptr;
+    PushLane lanes[2];
+    int lane_next = 0;
+    cudaStream_t tail_st = nullptr;  // ordering, formatting, statistics, result copies
     int2* d_yx = nullptr;
     int yx_cap = 0;
     size_t device_bytes = 0;
@@ -173,11 +184,18 @@ void free_all(lpf_stream* s) {
     if (!s) return;
     cudaSetDevice(s->dev);
     if (s->st) cudaStreamSynchronize(s->st);
+    if (s->tail_st) cudaStreamSynchronize(s->tail_st);
     void* ptrs[] = {s->ring, s->resring, s->D, s->xkeys, s->xvals, s->stage, s->d_lag, s->d_chg, s->d_member_start, s->d_member_ord,
-                    s->d_ord2d, s->d_dmax, s->keys[0], s->keys[1], s->vals[0], s->vals[1],
-                    s->d_counter, s->d_hist, s->d_partials, s->d_yx};
+                    s->d_ord2d, s->d_dmax, s->d_yx};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    for (auto& L : s->lanes) {
+        void* lp[] = {L.keys[0], L.keys[1], L.vals[0], L.vals[1], L.counter, L.hist, L.partials};
+        for (void* p : lp)
+            if (p) cudaFree(p);
+        if (L.lmax_done) cudaEventDestroy(L.lmax_done);
+        if (L.tail_done) cudaEventDestroy(L.tail_done);
+    }
     for (int i = 0; i < kMaxSlots; ++i) {
         if (s->slots[i].d_out) cudaFree(s->slots[i].d_out);
         if (s->slots[i].d_stats) cudaFree(s->slots[i].d_stats);
@@ -208,6 +226,7 @@ void free_all(lpf_stream* s) {
         cudaStreamDestroy(s->h2d_st);
     }
     if (s->copy_st) cudaStreamDestroy(s->copy_st);
+    if (s->tail_st) cudaStreamDestroy(s->tail_st);
     if (s->own_stream && s->st) cudaStreamDestroy(s->st);
 }
 
@@ -361,7 +380,7 @@ void launch_residual(lpf_stream* s, int64_t slot) {
         lpf::k_residual<15, TS><<<grid, lpf::ResGeom<15>::NT, lpf::residual_smem_bytes<15>(), s->st>>>(raw, res, s->H, s->W, s->P, seg_rows);
 }
 
-lpf::ResArgs res_args(lpf_stream* s, const lpf::FilterArgs& a, int Tmod) {
+lpf::ResArgs res_args(lpf_stream* s, const lpf::FilterArgs& a, int Tmod, const PushLane& L) {
     lpf::ResArgs ra;
     ra.a = a;
     ra.ring = s->ring;
@@ -371,15 +390,15 @@ lpf::ResArgs res_args(lpf_stream* s, const lpf::FilterArgs& a, int Tmod) {
     ra.Tmod = Tmod;
     ra.xkeys = s->xkeys;
     ra.xvals = s->xvals;
-    ra.xcounter = reinterpret_cast<unsigned long long*>(s->d_counter + 2);
+    ra.xcounter = reinterpret_cast<unsigned long long*>(L.counter + 2);
     ra.xcap = s->xcap;
     ra.band_k = s->prm.mode == LPF_MODE_SUBBAND ? s->prm.lmax_r : 0;
     return ra;
 }
 
 template <typename TS>
-void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows, int Tmod) {
-    const lpf::ResArgs ra = res_args(s, a, Tmod);
+void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows, int Tmod, const PushLane& L) {
+    const lpf::ResArgs ra = res_args(s, a, Tmod, L);
     dim3 grid((unsigned)s->n_strips, (unsigned)n_rows, (unsigned)s->fseg);
     if (s->prm.box_r == 7)
         lpf::k_filter_res<7, TS><<<grid, lpf::FiltGeom<7>::NT, lpf::res_filter_smem_bytes<7>(), s->st>>>(ra);
@@ -388,11 +407,11 @@ void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows, int 
 }
 
 template <typename TS>
-void launch_lmax_res(lpf_stream* s, const lpf::FilterArgs& a, int Tmod) {
+void launch_lmax_res(lpf_stream* s, const lpf::FilterArgs& a, int Tmod, const PushLane& L) {
     if (s->prm.mode == LPF_MODE_SUBBAND)
-        lpf::k_lmax_res<TS, true><<<148 * 8, 256, 0, s->st>>>(res_args(s, a, Tmod));
+        lpf::k_lmax_res<TS, true><<<148 * 8, 256, 0, s->st>>>(res_args(s, a, Tmod, L));
     else
-        lpf::k_lmax_res<TS, false><<<148 * 8, 256, 0, s->st>>>(res_args(s, a, Tmod));
+        lpf::k_lmax_res<TS, false><<<148 * 8, 256, 0, s->st>>>(res_args(s, a, Tmod, L));
 }
 
 template <typename TS>
@@ -475,8 +494,8 @@ size_t filter_smem_bytes(int r, int rmax) {
     return floats * sizeof(float);
 }
 
-void prof_mark(lpf_stream* s, int sl, int i) {
-    if (s->profiling) cudaEventRecord(s->ev[sl][i], s->st);
+void prof_mark(lpf_stream* s, int sl, int i, cudaStream_t st = nullptr) {
+    if (s->profiling) cudaEventRecord(s->ev[sl][i], st ? st : s->st);
 }
 
 // Accumulate the stage times of a finished slot (its done event has completed).
@@ -500,6 +519,8 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
     const int64_t ring_slot = T % s->depth;
     const int Tmod = (int)ring_slot;
     const int n_rows = n_active_rows(s, T);
+    const int p = s->lane_next;
+    PushLane& L = s->lanes[p];
     cudaGetLastError();
 
     prof_mark(s, sl, ST_INGEST);
@@ -523,7 +544,9 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
             default: launch_residual<__nv_bfloat16>(s, ring_slot); break;
         }
     }
-    lpf::k_zero_u32<<<1, 32, 0, s->st>>>(s->d_counter, 4);   // candidates, crossings (u64 at word 2)
+    // this lane's buffers were last used by the push two back: its tail must be done
+    LPF_TRY(cudaStreamWaitEvent(s->st, L.tail_done, 0));
+    lpf::k_zero_u32<<<1, 32, 0, s->st>>>(L.counter, 4);   // candidates, crossings (u64 at word 2)
     prof_mark(s, sl, ST_DEDISP);
     // images the filter reads: D - C per distinct delay row, or (per-subband
     // detector) the residual planes of the newest frame, in place for FP32
@@ -585,16 +608,16 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
         a.D = filter_images; a.P = s->P; a.H = s->H; a.W = s->W; a.r = s->prm.box_r; a.kappa = s->prm.kappa;
         a.tiles_x = s->tiles_x; a.tiles_y = s->tiles_y;
         a.member_start = s->d_member_start; a.member_ord = s->d_member_ord;
-        a.keys = s->keys[0]; a.vals = s->vals[0]; a.counter = s->d_counter; a.cap = s->prm.cand_cap;
-        a.bx = s->bx; a.by = s->by; a.partials = s->d_partials;
+        a.keys = L.keys[0]; a.vals = L.vals[0]; a.counter = L.counter; a.cap = s->prm.cand_cap;
+        a.bx = s->bx; a.by = s->by; a.partials = L.partials;
         if (clip) {
             lpf::k_clip_emit<<<dim3((unsigned)n_filter_blocks(s), (unsigned)s->F), 256, 0, s->st>>>(
                 ca, a, s->prm.lmax_r);
         } else if (s->stream_filter) {
             switch (s->prm.dtype) {
-                case LPF_FP32: launch_filter_res<float>(s, a, n_rows, Tmod); break;
-                case LPF_FP16: launch_filter_res<__half>(s, a, n_rows, Tmod); break;
-                default: launch_filter_res<__nv_bfloat16>(s, a, n_rows, Tmod); break;
+                case LPF_FP32: launch_filter_res<float>(s, a, n_rows, Tmod, L); break;
+                case LPF_FP16: launch_filter_res<__half>(s, a, n_rows, Tmod, L); break;
+                default: launch_filter_res<__nv_bfloat16>(s, a, n_rows, Tmod, L); break;
             }
         } else {
             dim3 grid((unsigned)(s->tiles_x * s->tiles_y), (unsigned)n_rows);
@@ -607,37 +630,46 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
     prof_mark(s, sl, ST_LMAX);
     if (n_rows > 0 && s->stream_filter && !clip) {
         switch (s->prm.dtype) {
-            case LPF_FP32: launch_lmax_res<float>(s, a, Tmod); break;
-            case LPF_FP16: launch_lmax_res<__half>(s, a, Tmod); break;
-            default: launch_lmax_res<__nv_bfloat16>(s, a, Tmod); break;
+            case LPF_FP32: launch_lmax_res<float>(s, a, Tmod, L); break;
+            case LPF_FP16: launch_lmax_res<__half>(s, a, Tmod, L); break;
+            default: launch_lmax_res<__nv_bfloat16>(s, a, Tmod, L); break;
         }
     }
-    prof_mark(s, sl, ST_SORT);
+    // the tail of this push on the tail stream, once its 3x3 pass and the tail of
+    // the previous push (same stream, other lane) are done; the main stream moves
+    // on to the next push's ingest and search
+    PushLane& Lprev = s->lanes[p ^ 1];
+    LPF_TRY(cudaStreamWaitEvent(s->st, Lprev.tail_done, 0));
+    LPF_TRY(cudaEventRecord(L.lmax_done, s->st));
+    cudaStream_t ts = s->tail_st;
+    LPF_TRY(cudaStreamWaitEvent(ts, L.lmax_done, 0));
+    prof_mark(s, sl, ST_SORT, ts);
     int cur = 0;
     for (int shift = 0; shift < s->key_bits; shift += 8) {
-        lpf::k_rs_hist<<<kSortBlocks, lpf::kSortThreads, 0, s->st>>>(s->keys[cur], s->d_counter,
-                                                                       s->prm.cand_cap, shift, s->d_hist);
-        lpf::k_rs_scan<<<1, 1024, 0, s->st>>>(s->d_hist, kSortBlocks);
-        lpf::k_rs_scatter<<<kSortBlocks, lpf::kSortThreads, 0, s->st>>>(
-            s->keys[cur], s->vals[cur], s->keys[cur ^ 1], s->vals[cur ^ 1], s->d_counter,
-            s->prm.cand_cap, shift, s->d_hist);
+        lpf::k_rs_hist<<<kSortBlocks, lpf::kSortThreads, 0, ts>>>(L.keys[cur], L.counter, s->prm.cand_cap, shift,
+                                                                 L.hist);
+        lpf::k_rs_scan<<<1, 1024, 0, ts>>>(L.hist, kSortBlocks);
+        lpf::k_rs_scatter<<<kSortBlocks, lpf::kSortThreads, 0, ts>>>(
+            L.keys[cur], L.vals[cur], L.keys[cur ^ 1], L.vals[cur ^ 1], L.counter, s->prm.cand_cap, shift, L.hist);
         cur ^= 1;
     }
-    prof_mark(s, sl, ST_FORMAT);
-    lpf::k_format<<<148 * 4, 256, 0, s->st>>>(s->keys[cur], s->vals[cur], s->d_counter, s->prm.cand_cap,
-                                              slot.d_out, s->d_ord2d, s->d_dmax, T, s->bx, s->by);
-    prof_mark(s, sl, ST_STATS);
+    prof_mark(s, sl, ST_FORMAT, ts);
+    lpf::k_format<<<148 * 4, 256, 0, ts>>>(L.keys[cur], L.vals[cur], L.counter, s->prm.cand_cap, slot.d_out,
+                                           s->d_ord2d, s->d_dmax, T, s->bx, s->by);
+    prof_mark(s, sl, ST_STATS, ts);
     if (n_rows > 0)
-        lpf::k_stats<<<n_rows, 256, 0, s->st>>>(s->d_partials, n_filter_blocks(s), slot.d_stats);
-    prof_mark(s, sl, ST_N);
+        lpf::k_stats<<<n_rows, 256, 0, ts>>>(L.partials, n_filter_blocks(s), slot.d_stats);
+    prof_mark(s, sl, ST_N, ts);
     if (cudaGetLastError() != cudaSuccess) return LPF_E_CUDA;
-    LPF_TRY(cudaMemcpyAsync(s->h_count + sl, s->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st));
+    LPF_TRY(cudaMemcpyAsync(s->h_count + sl, L.counter, sizeof(unsigned), cudaMemcpyDeviceToHost, ts));
     if (s->prm.qc)
-        LPF_TRY(cudaMemcpyAsync(s->h_qc + sl, slot.d_qc, sizeof(lpf::QcRecord), cudaMemcpyDeviceToHost, s->st));
+        LPF_TRY(cudaMemcpyAsync(s->h_qc + sl, slot.d_qc, sizeof(lpf::QcRecord), cudaMemcpyDeviceToHost, ts));
     if (n_rows > 0)
         LPF_TRY(cudaMemcpyAsync(s->h_stats + (size_t)sl * s->n_distinct * 3, slot.d_stats,
-                                (size_t)n_rows * 3 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
-    LPF_TRY(cudaEventRecord(slot.done, s->st));
+                                (size_t)n_rows * 3 * sizeof(double), cudaMemcpyDeviceToHost, ts));
+    LPF_TRY(cudaEventRecord(L.tail_done, ts));
+    LPF_TRY(cudaEventRecord(slot.done, ts));
+    s->lane_next = p ^ 1;
     s->prof_slot[sl] = s->profiling;
     slot.T = T;
     slot.n_active = n_rows;
@@ -805,8 +837,9 @@ size_t footprint_bytes(const lpf_stream* s) {
         t += (size_t)s->n_slots * b(sizeof(lpf::QcRecord));
     }
     t += b(s->member_start.size() * 4) + b(s->member_ord.size() * 4) + 2 * b((size_t)s->n_dm * 4);
-    t += 2 * (b(cap * 8) + b(cap * 4)) + b(16) + b((size_t)256 * kSortBlocks * 4);
-    t += b(nd * n_filter_blocks(s) * 3 * 8);
+    // two push lanes: keys and values (x2 for the sort), counter, histograms, partials
+    t += 2 * (2 * (b(cap * 8) + b(cap * 4)) + b(16) + b((size_t)256 * kSortBlocks * 4) +
+              b(nd * n_filter_blocks(s) * 3 * 8));
     t += (size_t)s->n_slots * (b(cap * sizeof(lpf::CandidateRec)) + b(nd * 3 * 8));
     return t;
 }
@@ -849,6 +882,7 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
     }
     if (cudaStreamCreateWithFlags(&s->copy_st, cudaStreamNonBlocking) != cudaSuccess) rc = LPF_E_CUDA;
     if (rc == LPF_OK && cudaStreamCreateWithFlags(&s->h2d_st, cudaStreamNonBlocking) != cudaSuccess) rc = LPF_E_CUDA;
+    if (rc == LPF_OK && cudaStreamCreateWithFlags(&s->tail_st, cudaStreamNonBlocking) != cudaSuccess) rc = LPF_E_CUDA;
     for (int i = 0; i < 2 && rc == LPF_OK; ++i)
         if (cudaEventCreateWithFlags(&s->stage_ready[i], cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&s->stage_free[i], cudaEventDisableTiming) != cudaSuccess)
@@ -881,13 +915,18 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_member_ord, s->member_ord.size());
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_ord2d, (size_t)s->n_dm);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_dmax, (size_t)s->n_dm);
-    for (int i = 0; i < 2 && rc == LPF_OK; ++i) {
-        rc = dev_alloc(s, &s->keys[i], (size_t)prm.cand_cap);
-        if (rc == LPF_OK) rc = dev_alloc(s, &s->vals[i], (size_t)prm.cand_cap);
+    for (auto& L : s->lanes) {
+        for (int i = 0; i < 2 && rc == LPF_OK; ++i) {
+            rc = dev_alloc(s, &L.keys[i], (size_t)prm.cand_cap);
+            if (rc == LPF_OK) rc = dev_alloc(s, &L.vals[i], (size_t)prm.cand_cap);
+        }
+        if (rc == LPF_OK) rc = dev_alloc(s, &L.counter, 4);
+        if (rc == LPF_OK) rc = dev_alloc(s, &L.hist, (size_t)256 * kSortBlocks);
+        if (rc == LPF_OK) rc = dev_alloc(s, &L.partials, (size_t)s->n_distinct * n_filter_blocks(s) * 3);
+        if (rc == LPF_OK && (cudaEventCreateWithFlags(&L.lmax_done, cudaEventDisableTiming) != cudaSuccess ||
+                             cudaEventCreateWithFlags(&L.tail_done, cudaEventDisableTiming) != cudaSuccess))
+            rc = LPF_E_CUDA;
     }
-    if (rc == LPF_OK) rc = dev_alloc(s, &s->d_counter, 4);
-    if (rc == LPF_OK) rc = dev_alloc(s, &s->d_hist, (size_t)256 * kSortBlocks);
-    if (rc == LPF_OK) rc = dev_alloc(s, &s->d_partials, (size_t)s->n_distinct * n_filter_blocks(s) * 3);
     for (int i = 0; i < s->n_slots && rc == LPF_OK; ++i) {
         rc = dev_alloc(s, &s->slots[i].d_out, (size_t)prm.cand_cap);
         if (rc == LPF_OK) rc = dev_alloc(s, &s->slots[i].d_stats, (size_t)s->n_distinct * 3);
@@ -1114,7 +1153,9 @@ int lpf_stream_info(const lpf_stream* s, lpf_stream_info_t* out) {
 int lpf_stream_sync(lpf_stream* s) {
     if (!s) return LPF_E_ARG;
     if (cudaSetDevice(s->dev) != cudaSuccess) return LPF_E_CUDA;
-    return cuda_fail(cudaStreamSynchronize(s->st));
+    int rc = cuda_fail(cudaStreamSynchronize(s->st));
+    if (rc == LPF_OK && s->tail_st) rc = cuda_fail(cudaStreamSynchronize(s->tail_st));
+    return rc;
 }
 
 int lpf_stream_close(lpf_stream* s) {
