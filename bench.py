@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-RESULT_SLOTS = 3                # frames in flight in the timed loops
+RESULT_SLOTS = 4                # result slots: up to 3 frames ahead of the oldest unpolled one
 METRIC = "pixel*DM-trials/s"
 WORKLOAD = "aartfaac-1024x1024-16sb-251dm-depth48-box31"
 
@@ -224,7 +224,6 @@ def run_reference(args):
 def run_ours(args):
     import torch
     import paper_2103_15418_b300 as lpf
-    from oracle import lpf_oracle as O   # host delay table for the byte counts only
 
     ws, rank, local = dist_env()
     dist = None
@@ -238,7 +237,7 @@ def run_ours(args):
     pool = [torch.from_numpy(st.frame(t)) for t in range(args.pool)]
     pool_dev = [p.to(dev) for p in pool]
     pool_pin = [p.pin_memory() for p in pool]
-    cur = torch.cuda.current_stream(dev)
+    cur = torch.cuda.Stream(dev)            # the search stream (the timing events are recorded on it)
     s = lpf.Stream(spec.H, spec.W, spec.freqs_mhz, spec.dm_grid, spec.depth, kappa=spec.kappa,
                    box_r=spec.box_r, dtype=args.dtype, result_slots=RESULT_SLOTS, cuda_stream=cur,
                    qc=args.qc, qc_min_frames=16)
@@ -271,15 +270,18 @@ def run_ours(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    # result_slots - 1 pushes ahead of the oldest unpolled frame, as in the
+    # end-to-end loop below
+    ahead = max(1, RESULT_SLOTS - 1)
     ev0.record(cur)
-    push(T)
-    T += 1
-    for k in range(1, args.steps):
+    for k in range(args.steps):
         push(T)
         T += 1
+        if k >= ahead:
+            poll()
+    for _ in range(ahead):
         poll()
     ev1.record(cur)
-    poll()
     torch.cuda.synchronize()
     clk = clocks.stop()
     s.set_profiling(False)
@@ -354,11 +356,11 @@ def run_ours(args):
               "traffic": traffic.get("k_filter_res"),
               "algorithmic_flop_per_launch": f_ops, "avg_launch_ms": f_ms, "launches_per_step": 1}
     roof = roof_f if f_ms >= dd_ms else roof_dd
-    # quality control + ingest (k_qc_scan, k_qc_decide, k_ingest_qc, k_residual): the
+    # quality control + ingest (k_qc_scan, k_qc_decide, k_residual, k_ingest_qc): the
     # QC passes read the frame and the running mean and m2 twice and write them once
     b = 4 if args.dtype == "fp32" else 2
     qc_bytes = spec.F * HW * (12 + 20 + b)
-    qc_ms = per_push["ingest"]
+    qc_ms = per_push["ingest"] + per_push.get("ring_write", 0.0)
     roof_qc = {"kernel": "quality control + ingest (k_qc_scan, k_qc_decide, k_ingest_qc, k_residual)",
                "bound": "hbm", "achieved": qc_bytes / (qc_ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                "frac": qc_bytes / (qc_ms / 1e3) / 1e9 / hbm_peak, "peak_source": peak_src, "traffic": None,
@@ -415,7 +417,7 @@ def run_subband(args):
     spec = synth.spec_aartfaac(dtype=args.dtype)
     st = synth.SyntheticStream(spec, seed=0)
     pool = [torch.from_numpy(st.frame(t)).cuda() for t in range(args.pool)]
-    cur = torch.cuda.current_stream()
+    cur = torch.cuda.Stream()               # the search stream (the timing events are recorded on it)
     s = lpf.Stream(spec.H, spec.W, spec.freqs_mhz, None, 2, kappa=spec.kappa, box_r=spec.box_r,
                    dtype=args.dtype, result_slots=RESULT_SLOTS, cuda_stream=cur, mode="subband", lmax_r=3,
                    clip_iters=args.clip_iters)

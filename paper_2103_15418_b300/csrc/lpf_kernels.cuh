@@ -57,6 +57,13 @@ __device__ __forceinline__ void st4(__nv_bfloat16* p, float4 v) {
 __device__ __forceinline__ void st1(float* p, float v) { *p = v; }
 __device__ __forceinline__ void st1(__half* p, float v) { *p = __float2half_rn(v); }
 __device__ __forceinline__ void st1(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+// v as the storage type TS holds it (round to nearest even, as st1 and st4 store)
+template <typename TS> __device__ __forceinline__ float as_stored(float v);
+template <> __device__ __forceinline__ float as_stored<float>(float v) { return v; }
+template <> __device__ __forceinline__ float as_stored<__half>(float v) { return __half2float(__float2half_rn(v)); }
+template <> __device__ __forceinline__ float as_stored<__nv_bfloat16>(float v) {
+    return __bfloat162float(__float2bfloat16_rn(v));
+}
 
 // ------------------------------------------------------------------ a2: ingest
 // Convert frame [F][HW] (FP32, caller layout) into ring slot [F][P] (storage type,

@@ -45,12 +45,15 @@ struct ResGeom {
 // k_residual: Xr = X - C(X) for the F planes of one ring slot, C the clipped box
 // mean of radius R (horizontal two-stack sums, vertical sliding sum, C by
 // reciprocal plus one Newton step against the exact count, so a constant
-// window gives Xr = 0 exactly).  X is read as stored (storage type TS) and Xr
-// is written in the storage type.  Grid: (strips, F, row segments); a segment
-// of seg_rows output rows streams from r rows above it (its vertical window
-// starts there) to r rows below it.
+// window gives Xr = 0 exactly).  X is read from the pushed frame [F][H][W]
+// (FP32) and rounded to the storage type TS, the value the raw ring holds; a
+// band whose bit is set in *drop (quality control) is all zeros.  Xr is written
+// in the storage type.  Grid: (strips, F, row segments); a segment of seg_rows
+// output rows streams from r rows above it (its vertical window starts there)
+// to r rows below it.
 template <int R, typename TS>
-__global__ void __launch_bounds__(ResGeom<R>::NT) k_residual(const TS* __restrict__ raw_slot,
+__global__ void __launch_bounds__(ResGeom<R>::NT) k_residual(const float* __restrict__ frame,
+                                                             const unsigned* __restrict__ drop,
                                                              TS* __restrict__ res_slot, int H, int W,
                                                              int64_t P, int seg_rows) {
     using G = ResGeom<R>;
@@ -61,11 +64,11 @@ __global__ void __launch_bounds__(ResGeom<R>::NT) k_residual(const TS* __restric
     __shared__ float2 rowC[B];
     const int strip = blockIdx.x, f = blockIdx.y;
     const int x0 = strip * TX;
-    const TS* X = raw_slot + (int64_t)f * P;
+    const float* X = frame + (int64_t)f * H * W;
     TS* Xr = res_slot + (int64_t)f * P;
     const int t = threadIdx.x;
     const int xl = x0 - R + t;                  // loaded column of this thread
-    const bool lcol = t < WD && xl >= 0 && xl < W;
+    const bool lcol = t < WD && xl >= 0 && xl < W && !(drop && ((*drop >> f) & 1u));
     const int xs = x0 + t;                      // output column of this thread
     const bool ocol = t < TX && xs < W;
     const int nx = ocol ? min(xs + R, W - 1) - max(xs - R, 0) + 1 : 0;
@@ -82,10 +85,10 @@ __global__ void __launch_bounds__(ResGeom<R>::NT) k_residual(const TS* __restric
         float(*cur)[SD] = Xb[k & 1];
         float(*prev)[SD] = Xb[(k + 1) & 1];
         if (t < WD) {
-            const TS* src = X + (int64_t)ybase * W + xl;
+            const float* src = X + (int64_t)ybase * W + xl;
 #pragma unroll
             for (int j = 0; j < B; ++j) {
-                cur[j][t] = (lcol && ybase + j < H) ? ld1(src) : 0.f;
+                cur[j][t] = (lcol && ybase + j < H) ? as_stored<TS>(__ldg(src)) : 0.f;
                 src += W;
             }
         }

@@ -31,8 +31,12 @@ constexpr double kCdmSeconds = 4.148808e3;   // s MHz^2 cm^3 / pc (Sec. 3.2)
 using lpf::kSortBlocks;
 constexpr int kMaxSlots = 16;
 
-enum Stage { ST_INGEST, ST_DEDISP, ST_FILTER, ST_LMAX, ST_SORT, ST_FORMAT, ST_STATS, ST_N };
-const char* kStageNames[ST_N] = {"ingest", "dedisperse", "filter_detect", "lmax", "sort", "format", "stats"};
+// Stages in the order their marks are recorded.  The residual path writes the
+// raw ring after the shift-sum (ring_write); the tiled and clipping paths write
+// it at ingest (ring_write then empty).
+enum Stage { ST_INGEST, ST_DEDISP, ST_RINGW, ST_FILTER, ST_LMAX, ST_SORT, ST_FORMAT, ST_STATS, ST_N };
+const char* kStageNames[ST_N] = {"ingest", "dedisperse", "ring_write", "filter_detect", "lmax", "sort", "format",
+                                 "stats"};
 
 int ceil_log2(int64_t v) {
     int b = 0;
@@ -49,7 +53,9 @@ struct PushLane {
     unsigned* counter = nullptr;       // [4]: candidates, -, crossings (u64 at word 2)
     unsigned* hist = nullptr;          // radix-sort block histograms
     double* partials = nullptr;        // [n_distinct][filter blocks][3]
-    cudaEvent_t lmax_done = nullptr;   // the push's 3x3 pass finished: its tail may start
+    cudaEvent_t filter_done = nullptr; // the push's filter finished: its tail may start
+    cudaEvent_t lmax_done = nullptr;   // the push's 3x3 pass finished: the raw ring slot it
+                                       // reads last and the crossing list may be rewritten
     cudaEvent_t tail_done = nullptr;   // the push's tail finished: the lane may be reused
 };
 
@@ -144,8 +150,8 @@ struct lpf_stream {
     int tiles_x = 0, tiles_y = 0;
     size_t filter_smem = 0;
     int filter_rmax = 16;
-    bool stream_filter = false;
-    int fseg = 1;                   // row segments per strip of the streaming filter     // residual path: k_residual + k_filter_res (box_r 7 or 15)
+    bool stream_filter = false;     // residual path: k_residual + k_filter_res (box_r 7 or 15)
+    int fseg = 1;                   // row segments per strip of the streaming filter
     void* resring = nullptr;        // [depth][F][P] per-subband residual X - C(X), storage type
     int n_strips = 0;
 
@@ -193,6 +199,7 @@ void free_all(lpf_stream* s) {
         void* lp[] = {L.keys[0], L.keys[1], L.vals[0], L.vals[1], L.counter, L.hist, L.partials};
         for (void* p : lp)
             if (p) cudaFree(p);
+        if (L.filter_done) cudaEventDestroy(L.filter_done);
         if (L.lmax_done) cudaEventDestroy(L.lmax_done);
         if (L.tail_done) cudaEventDestroy(L.tail_done);
     }
@@ -362,8 +369,8 @@ void launch_ingest(lpf_stream* s, const float* frame, int64_t slot) {
 }
 
 template <typename TS>
-void launch_residual(lpf_stream* s, int64_t slot) {
-    const TS* raw = reinterpret_cast<const TS*>(s->ring) + slot * s->F * s->P;
+void launch_residual(lpf_stream* s, const float* frame, int64_t slot) {
+    const unsigned* drop = s->prm.qc ? s->qc_words + 1 : nullptr;
     TS* res = reinterpret_cast<TS*>(s->resring) + slot * s->F * s->P;
     // row segments so that about two waves of CTAs (4 per SM) run; a segment
     // keeps at least 4 row blocks so that its 2r halo rows stay a small share
@@ -375,9 +382,11 @@ void launch_residual(lpf_stream* s, int64_t slot) {
     nseg = (s->H + seg_rows - 1) / seg_rows;
     dim3 grid((unsigned)s->n_strips, (unsigned)s->F, (unsigned)nseg);
     if (s->prm.box_r == 7)
-        lpf::k_residual<7, TS><<<grid, lpf::ResGeom<7>::NT, lpf::residual_smem_bytes<7>(), s->st>>>(raw, res, s->H, s->W, s->P, seg_rows);
+        lpf::k_residual<7, TS><<<grid, lpf::ResGeom<7>::NT, lpf::residual_smem_bytes<7>(), s->st>>>(
+            frame, drop, res, s->H, s->W, s->P, seg_rows);
     else
-        lpf::k_residual<15, TS><<<grid, lpf::ResGeom<15>::NT, lpf::residual_smem_bytes<15>(), s->st>>>(raw, res, s->H, s->W, s->P, seg_rows);
+        lpf::k_residual<15, TS><<<grid, lpf::ResGeom<15>::NT, lpf::residual_smem_bytes<15>(), s->st>>>(
+            frame, drop, res, s->H, s->W, s->P, seg_rows);
 }
 
 lpf::ResArgs res_args(lpf_stream* s, const lpf::FilterArgs& a, int Tmod, const PushLane& L) {
@@ -407,11 +416,11 @@ void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows, int 
 }
 
 template <typename TS>
-void launch_lmax_res(lpf_stream* s, const lpf::FilterArgs& a, int Tmod, const PushLane& L) {
+void launch_lmax_res(lpf_stream* s, const lpf::FilterArgs& a, int Tmod, const PushLane& L, cudaStream_t st) {
     if (s->prm.mode == LPF_MODE_SUBBAND)
-        lpf::k_lmax_res<TS, true><<<148 * 8, 256, 0, s->st>>>(res_args(s, a, Tmod, L));
+        lpf::k_lmax_res<TS, true><<<148 * 8, 256, 0, st>>>(res_args(s, a, Tmod, L));
     else
-        lpf::k_lmax_res<TS, false><<<148 * 8, 256, 0, s->st>>>(res_args(s, a, Tmod, L));
+        lpf::k_lmax_res<TS, false><<<148 * 8, 256, 0, st>>>(res_args(s, a, Tmod, L));
 }
 
 template <typename TS>
@@ -531,18 +540,28 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
         lpf::k_qc_decide<<<1, 32, 0, s->st>>>(s->qc_part, s->F, s->HW, s->prm.qc_z, s->qc_words, s->qc_n,
                                               s->qc_invn, s->qc_words + 1, slot.d_qc);
     }
-    switch (s->prm.dtype) {
-        case LPF_FP32: launch_ingest<float>(s, frame_dev, ring_slot); break;
-        case LPF_FP16: launch_ingest<__half>(s, frame_dev, ring_slot); break;
-        default: launch_ingest<__nv_bfloat16>(s, frame_dev, ring_slot); break;
-    }
-    const bool clip = s->prm.clip_iters > 1;
-    if (s->stream_filter && !clip) {
+    auto ingest = [&]() {
         switch (s->prm.dtype) {
-            case LPF_FP32: launch_residual<float>(s, ring_slot); break;
-            case LPF_FP16: launch_residual<__half>(s, ring_slot); break;
-            default: launch_residual<__nv_bfloat16>(s, ring_slot); break;
+            case LPF_FP32: launch_ingest<float>(s, frame_dev, ring_slot); break;
+            case LPF_FP16: launch_ingest<__half>(s, frame_dev, ring_slot); break;
+            default: launch_ingest<__nv_bfloat16>(s, frame_dev, ring_slot); break;
         }
+    };
+    const bool clip = s->prm.clip_iters > 1;
+    // Residual path: the residuals and their shift-sum come from the pushed frame
+    // and the residual ring, so the raw ring write of this frame waits until after
+    // the shift-sum; by then the previous push's 3x3 pass (tail stream), which may
+    // read the frame this write replaces, has long finished.
+    const bool late_ring = s->stream_filter && !clip;
+    PushLane& Lprev = s->lanes[p ^ 1];
+    if (late_ring) {
+        switch (s->prm.dtype) {
+            case LPF_FP32: launch_residual<float>(s, frame_dev, ring_slot); break;
+            case LPF_FP16: launch_residual<__half>(s, frame_dev, ring_slot); break;
+            default: launch_residual<__nv_bfloat16>(s, frame_dev, ring_slot); break;
+        }
+    } else {
+        ingest();
     }
     // this lane's buffers were last used by the push two back: its tail must be done
     LPF_TRY(cudaStreamWaitEvent(s->st, L.tail_done, 0));
@@ -602,6 +621,12 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
             default: launch_dedisperse<__nv_bfloat16>(s, n_rows, Tmod); break;
         }
     }
+    prof_mark(s, sl, ST_RINGW);
+    if (late_ring) {
+        // the previous 3x3 pass also reads the crossing list the filter rewrites
+        LPF_TRY(cudaStreamWaitEvent(s->st, Lprev.lmax_done, 0));
+        ingest();
+    }
     prof_mark(s, sl, ST_FILTER);
     lpf::FilterArgs a;
     if (n_rows > 0) {
@@ -627,22 +652,22 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
                 lpf::k_filter<16><<<grid, lpf::kFilterThreads, s->filter_smem, s->st>>>(a);
         }
     }
-    prof_mark(s, sl, ST_LMAX);
-    if (n_rows > 0 && s->stream_filter && !clip) {
+    // the tail of this push (3x3 pass, ordering, formatting, statistics, copies)
+    // on the tail stream once its filter is done, after the tail of the previous
+    // push (same stream, other lane); the main stream moves on to the next push's
+    // residuals and shift-sum
+    LPF_TRY(cudaEventRecord(L.filter_done, s->st));
+    cudaStream_t ts = s->tail_st;
+    LPF_TRY(cudaStreamWaitEvent(ts, L.filter_done, 0));
+    prof_mark(s, sl, ST_LMAX, ts);
+    if (n_rows > 0 && late_ring) {
         switch (s->prm.dtype) {
-            case LPF_FP32: launch_lmax_res<float>(s, a, Tmod, L); break;
-            case LPF_FP16: launch_lmax_res<__half>(s, a, Tmod, L); break;
-            default: launch_lmax_res<__nv_bfloat16>(s, a, Tmod, L); break;
+            case LPF_FP32: launch_lmax_res<float>(s, a, Tmod, L, ts); break;
+            case LPF_FP16: launch_lmax_res<__half>(s, a, Tmod, L, ts); break;
+            default: launch_lmax_res<__nv_bfloat16>(s, a, Tmod, L, ts); break;
         }
     }
-    // the tail of this push on the tail stream, once its 3x3 pass and the tail of
-    // the previous push (same stream, other lane) are done; the main stream moves
-    // on to the next push's ingest and search
-    PushLane& Lprev = s->lanes[p ^ 1];
-    LPF_TRY(cudaStreamWaitEvent(s->st, Lprev.tail_done, 0));
-    LPF_TRY(cudaEventRecord(L.lmax_done, s->st));
-    cudaStream_t ts = s->tail_st;
-    LPF_TRY(cudaStreamWaitEvent(ts, L.lmax_done, 0));
+    LPF_TRY(cudaEventRecord(L.lmax_done, ts));
     prof_mark(s, sl, ST_SORT, ts);
     int cur = 0;
     for (int shift = 0; shift < s->key_bits; shift += 8) {
@@ -882,6 +907,8 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
     }
     if (cudaStreamCreateWithFlags(&s->copy_st, cudaStreamNonBlocking) != cudaSuccess) rc = LPF_E_CUDA;
     if (rc == LPF_OK && cudaStreamCreateWithFlags(&s->h2d_st, cudaStreamNonBlocking) != cudaSuccess) rc = LPF_E_CUDA;
+    // default priority: a higher one lets the tail's blocks take SMs ahead of the
+    // next push's residuals and shift-sum, which then finish later (measured)
     if (rc == LPF_OK && cudaStreamCreateWithFlags(&s->tail_st, cudaStreamNonBlocking) != cudaSuccess) rc = LPF_E_CUDA;
     for (int i = 0; i < 2 && rc == LPF_OK; ++i)
         if (cudaEventCreateWithFlags(&s->stage_ready[i], cudaEventDisableTiming) != cudaSuccess ||
@@ -923,7 +950,8 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
         if (rc == LPF_OK) rc = dev_alloc(s, &L.counter, 4);
         if (rc == LPF_OK) rc = dev_alloc(s, &L.hist, (size_t)256 * kSortBlocks);
         if (rc == LPF_OK) rc = dev_alloc(s, &L.partials, (size_t)s->n_distinct * n_filter_blocks(s) * 3);
-        if (rc == LPF_OK && (cudaEventCreateWithFlags(&L.lmax_done, cudaEventDisableTiming) != cudaSuccess ||
+        if (rc == LPF_OK && (cudaEventCreateWithFlags(&L.filter_done, cudaEventDisableTiming) != cudaSuccess ||
+                             cudaEventCreateWithFlags(&L.lmax_done, cudaEventDisableTiming) != cudaSuccess ||
                              cudaEventCreateWithFlags(&L.tail_done, cudaEventDisableTiming) != cudaSuccess))
             rc = LPF_E_CUDA;
     }
