@@ -22,7 +22,8 @@ method, each citing the passage of Ruhe et al. (arXiv 2103.15418) it follows:
                    for rings that store those residuals in reduced precision
   subband_detect   Sec. 2.1.1-2.1.2 on every band image, (2k+1)^2 maximum (k = 3)
   clip_detect      Sec. 2.1.1 iterated: C and S re-estimated from the pixels not
-                   yet flagged, until no new flag or the iteration limit
+                   yet flagged, until no new flag or the iteration limit; the
+                   uniform box or the Gaussian kernel G(n, m, s) (kernel_sum)
   qc_band_scores   App. A, z = (b - median(b)) / MAD(b) of the band-image means
   QCState, qc_frame  App. A, per-pixel running mean / standard deviation
                    (Welford) and scores zeta; bands over either threshold are
@@ -34,6 +35,9 @@ Readings where the paper is silent or garbled (all listed in the design doc):
     delay is >= 0; delays are rounded half up, floor(x + 0.5), in FP64.
   * The kernel is the square uniform box of radius r, truncated at the image
     edge and normalised by the number of in-image pixels (Z of Sec. 2.1.1).
+    The Gaussian kernel G(n, m, s) (per-subband detector) has the same square
+    (2r+1)^2 support (the window of Z's double sum) and is normalised by the
+    sum of its weights over the in-image window pixels.
   * The spread is two-pass: (D - C)^2 uses C at each window pixel.
   * The local maximum is taken on the dedispersed image over the 3x3 window
     clipped to the image; ties count as maxima (x = max).
@@ -139,6 +143,38 @@ def window_sum_1d(a: np.ndarray, r: int, axis: int) -> np.ndarray:
 def box_sum(img: np.ndarray, r: int) -> np.ndarray:
     """sum over the (2r+1)^2 square window clipped to the image (double sum, rows then columns)."""
     return window_sum_1d(window_sum_1d(img, r, axis=1), r, axis=0)
+
+
+def kernel_factors(r: int, s: Optional[float] = None) -> np.ndarray:
+    """g(i), i = -r..r: the Gaussian kernel of Sec. 2.1.1 on the (2r+1)^2 window is
+    G(n, m, s) = g(n) g(m) / Z with g(i) = exp(-i^2 / (2 s^2)), since
+    exp(-(n^2 + m^2) / (2 s^2)) factorises; s = None is the uniform box (g = 1)."""
+    i = np.arange(-r, r + 1, dtype=np.float64)
+    if s is None:
+        return np.ones_like(i)
+    return np.exp(-(i * i) / (2.0 * float(s) * float(s)))
+
+
+def kernel_sum(img: np.ndarray, r: int, s: Optional[float] = None) -> np.ndarray:
+    """sum_q g(qy - py) g(qx - px) img(q) over the (2r+1)^2 window clipped to the
+    image, unnormalised (rows then columns); s = None gives box_sum."""
+    g = kernel_factors(r, s)
+    out = np.asarray(img, dtype=np.float64)
+    for axis in (1, 0):
+        a = out
+        n = a.shape[axis]
+        out = np.zeros_like(a)
+        for k in range(-r, r + 1):
+            dst = [slice(None)] * a.ndim
+            src = [slice(None)] * a.ndim
+            if k >= 0:
+                dst[axis] = slice(0, max(n - k, 0))
+                src[axis] = slice(k, n)
+            else:
+                dst[axis] = slice(-k, n)
+                src[axis] = slice(0, max(n + k, 0))
+            out[tuple(dst)] += g[k + r] * a[tuple(src)]
+    return out
 
 
 def window_count(H: int, W: int, r: int) -> np.ndarray:
@@ -399,13 +435,16 @@ def subband_detect(frame: np.ndarray, r: int, kappa: float, k: int = 3):
     return cands, stats, maps
 
 
-def clip_detect(D: np.ndarray, r: int, kappa: float, k: int = 1, iters: int = 1) -> Dict[str, np.ndarray]:
+def clip_detect(D: np.ndarray, r: int, kappa: float, k: int = 1, iters: int = 1,
+                s: Optional[float] = None) -> Dict[str, np.ndarray]:
     """Iterated sigma clipping of one image (Sec. 2.1.1): at each iteration C and S
-    are the box means over the window pixels not yet flagged (the count of those
-    pixels normalises), y = I(snr > kappa) is added to the flags, and the loop
-    stops when an iteration flags no new pixel or after iters iterations.  The
-    peaks are the (2k+1)^2 maxima of D among the flagged pixels (Sec. 2.1.2); the
-    S/N is that of the last iteration.  iters = 1 is detect().
+    are the kernel-weighted means over the window pixels not yet flagged (the
+    kernel weight of those pixels normalises: Z restricted to them), y = I(snr >
+    kappa) is added to the flags, and the loop stops when an iteration flags no
+    new pixel or after iters iterations.  The peaks are the (2k+1)^2 maxima of D
+    among the flagged pixels (Sec. 2.1.2); the S/N is that of the last iteration.
+    The kernel is the Gaussian G(n, m, s) on the (2r+1)^2 window, or the uniform
+    box for s = None; iters = 1 with the box is detect().
     """
     D = np.asarray(D, np.float64)
     flags = np.zeros(D.shape, bool)
@@ -413,12 +452,12 @@ def clip_detect(D: np.ndarray, r: int, kappa: float, k: int = 1, iters: int = 1)
     n = None
     for _ in range(max(int(iters), 1)):
         m = (~flags).astype(np.float64)
-        n = box_sum(m, r)
+        n = kernel_sum(m, r, s)
         ok = n > 0
         C = np.zeros_like(D)
-        C[ok] = box_sum(D * m, r)[ok] / n[ok]
+        C[ok] = kernel_sum(D * m, r, s)[ok] / n[ok]
         S = np.zeros_like(D)
-        S[ok] = box_sum((D - C) ** 2 * m, r)[ok] / n[ok]
+        S[ok] = kernel_sum((D - C) ** 2 * m, r, s)[ok] / n[ok]
         snr = snr_map(D, C, S)
         above = snr > kappa
         new = above & ~flags

@@ -609,3 +609,82 @@ def test_clip_unmasks_a_faint_source_beside_a_bright_one():
     # the loop stops once nothing new is flagged: more iterations change nothing
     more = O.clip_detect(D, 7, 6.0, k=1, iters=12)
     assert np.array_equal(more["mask"], many["mask"]) and np.array_equal(more["flags"], many["flags"])
+
+
+# ----------------------------------------------------------------- Gaussian kernel G(n, m, s) (Sec. 2.1.1)
+def test_gauss_kernel_delta_response_is_the_normalised_kernel():
+    """A unit delta at p0: wherever the window lies inside the image, C(p) =
+    exp(-|p - p0|^2 / (2 s^2)) / Z, Z the unnormalised kernel summed over the
+    (2r+1)^2 window (the 2-D form, not its factors); zero beyond r."""
+    H, W, r, s = 41, 37, 5, 1.7
+    D = np.zeros((H, W))
+    y0, x0 = 20, 18
+    D[y0, x0] = 1.0
+    Z = sum(math.exp(-(i * i + j * j) / (2 * s * s)) for i in range(-r, r + 1) for j in range(-r, r + 1))
+    C = O.clip_detect(D, r, 1e9, iters=1, s=s)["C"]
+    for dy in range(-r - 2, r + 3):
+        for dx in range(-r - 2, r + 3):
+            inside = abs(dy) <= r and abs(dx) <= r
+            want = math.exp(-(dy * dy + dx * dx) / (2 * s * s)) / Z if inside else 0.0
+            assert abs(C[y0 + dy, x0 + dx] - want) < 1e-15 + 1e-12 * want, (dy, dx)
+
+
+def test_gauss_kernel_reproduces_an_affine_image_inside():
+    """G is symmetric, so G * (a + b y + c x) is the image itself wherever the window
+    is whole, and S = 0 where every window pixel's C is exact; at an edge the
+    truncated window is lopsided and C departs from the image."""
+    H, W, r, s = 40, 44, 4, 2.5
+    yy, xx = np.mgrid[:H, :W]
+    D = 3.0 + 0.7 * yy - 1.3 * xx
+    res = O.clip_detect(D, r, 6.0, iters=1, s=s)
+    inner = (slice(r, H - r), slice(r, W - r))
+    assert np.allclose(res["C"][inner], D[inner], rtol=0, atol=1e-10)
+    core = (slice(2 * r, H - 2 * r), slice(2 * r, W - 2 * r))
+    assert np.all(res["S"][core] < 1e-18)
+    assert abs(res["C"][0, 20] - D[0, 20]) > 0.5
+
+
+def test_gauss_kernel_masked_means_by_brute_force():
+    """Second iteration with the Gaussian kernel, image edges included: C and S at
+    every pixel are the means over the unflagged in-image window pixels, each
+    weighted by exp(-(dy^2 + dx^2) / (2 s^2)) taken whole.  A lone delta reaches
+    at most sqrt(Z) = 3.47 here, hence kappa = 3."""
+    rng = np.random.default_rng(23)
+    D = rng.standard_normal((13, 11))
+    D[5, 4] += 60.0
+    D[9, 8] += 45.0
+    r, s, kappa = 3, 1.4, 3.0
+    first = O.clip_detect(D, r, kappa, iters=1, s=s)
+    flags = first["snr"] > kappa
+    assert flags[5, 4] and flags[9, 8] and flags.sum() == 2
+    second = O.clip_detect(D, r, kappa, iters=2, s=s)
+    H, W = D.shape
+
+    def wmean(y, x, val):
+        num = den = 0.0
+        for yy in range(max(0, y - r), min(H, y + r + 1)):
+            for xx in range(max(0, x - r), min(W, x + r + 1)):
+                if not flags[yy, xx]:
+                    w = math.exp(-((yy - y) ** 2 + (xx - x) ** 2) / (2 * s * s))
+                    num += w * val(yy, xx)
+                    den += w
+        return num / den
+
+    for y in range(H):
+        for x in range(W):
+            assert abs(second["C"][y, x] - wmean(y, x, lambda a, b: D[a, b])) < 1e-12
+            sq = wmean(y, x, lambda a, b: (D[a, b] - second["C"][a, b]) ** 2)
+            assert abs(second["S"][y, x] - sq) < 1e-12 * max(1.0, sq)
+
+
+def test_gauss_kernel_wide_limit_is_the_box():
+    """s -> infinity: every weight tends to 1 and the Gaussian detector becomes the
+    box detector (masks equal, S/N to 1e-9), through three clipping iterations."""
+    rng = np.random.default_rng(24)
+    D = rng.standard_normal((30, 26))
+    D[12, 9] += 30.0
+    D[20, 18] += 12.0
+    a = O.clip_detect(D, 4, 4.0, k=2, iters=3, s=1e7)
+    b = O.clip_detect(D, 4, 4.0, k=2, iters=3)
+    assert np.array_equal(a["mask"], b["mask"]) and a["mask"].any()
+    assert np.allclose(a["snr"], b["snr"], rtol=0, atol=1e-9)
