@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--pool", type=int, default=12, help="distinct synthetic frames cycled")
     ap.add_argument("--clip-iters", type=int, default=1,
                     help="subband workload: sigma-clip iterations (1 = one pass)")
+    ap.add_argument("--gauss-sigma", type=float, default=0.0,
+                    help="subband workload: Gaussian background kernel of this width in pixels on the "
+                         "31x31 window (0 = the uniform box)")
     ap.add_argument("--qc", action="store_true",
                     help="quality control of every frame before the search (band and pixel scores)")
     ap.add_argument("--workload", default="aartfaac", choices=["aartfaac", "serving", "subband"],
@@ -410,7 +413,8 @@ def _passes(spec):
 
 def run_subband(args):
     """The paper's per-subband detector on the AARTFAAC stream (1024^2, 16 bands,
-    31x31 box, 7x7 maximum): every band image of every frame, device-timed."""
+    31x31 window, uniform box or Gaussian kernel, 7x7 maximum): every band image of
+    every frame, device-timed."""
     import torch
     import paper_2103_15418_b300 as lpf
     import synth
@@ -420,7 +424,8 @@ def run_subband(args):
     cur = torch.cuda.Stream()               # the search stream (the timing events are recorded on it)
     s = lpf.Stream(spec.H, spec.W, spec.freqs_mhz, None, 2, kappa=spec.kappa, box_r=spec.box_r,
                    dtype=args.dtype, result_slots=RESULT_SLOTS, cuda_stream=cur, mode="subband", lmax_r=3,
-                   clip_iters=args.clip_iters)
+                   clip_iters=args.clip_iters, kernel="gauss" if args.gauss_sigma > 0 else "box",
+                   gauss_sigma=args.gauss_sigma)
     T = 0
     for _ in range(args.warmup + 2):
         s.push(pool[T % args.pool], T)
@@ -437,9 +442,9 @@ def run_subband(args):
         T += 1
         if k >= RESULT_SLOTS - 1:
             ncand.append(s.poll(timeout_ms=600000)[2])
-    ev1.record(cur)
     while len(ncand) < args.steps:
         ncand.append(s.poll(timeout_ms=600000)[2])
+    ev1.record(cur)
     torch.cuda.synchronize()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     kt = s.kernel_times(reset=True)
@@ -448,8 +453,9 @@ def run_subband(args):
     px = spec.H * spec.W * spec.F
     print(json.dumps({
         "metric": "pixel*bands/s", "value": px * args.steps / elapsed, "unit": "pixel*bands/s",
-        "workload": "subband-detector-1024x1024-16bands-box31-max7x7", "storage": args.dtype,
-        "clip_iters": args.clip_iters,
+        "workload": "subband-detector-1024x1024-16bands-" +
+                    (f"gauss{args.gauss_sigma:g}-window31" if args.gauss_sigma > 0 else "box31") + "-max7x7",
+        "storage": args.dtype, "clip_iters": args.clip_iters,
         "steps": args.steps, "ms_per_step": 1e3 * elapsed / args.steps,
         "kernel_ms_per_step": per_push, "candidates_per_step": float(np.mean(ncand)),
         "data": "synthetic (seeded AARTFAAC-shaped stream)"}), flush=True)

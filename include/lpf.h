@@ -59,6 +59,11 @@ extern "C" {
 #define LPF_MODE_DISPERSED 0   /* the dispersed-transient search over the DM trials (Sec. 2.1, App. B.2) */
 #define LPF_MODE_SUBBAND   1   /* the per-subband detector: every band image of the frame (Sec. 2.1.1-2.1.2) */
 
+/* background kernel G of the centre / spread filter (Sec. 2.1.1) */
+#define LPF_KERNEL_BOX     0   /* uniform square box of radius box_r                          */
+#define LPF_KERNEL_GAUSS   1   /* G(n, m, s) = exp(-(n^2 + m^2) / (2 s^2)) / Z on the (2 box_r + 1)^2
+                                  window; per-subband detector only                          */
+
 /* storage type of the ring buffer (arithmetic is always FP32) */
 #define LPF_FP32 0
 #define LPF_FP16 1
@@ -102,6 +107,13 @@ typedef struct {
      * + 1)^2 maxima of X_f, with the S/N of the last iteration.  1 = one pass
      * (the residual filter).                                                    */
     int    clip_iters;    /* 1..16 (> 1 only with LPF_MODE_SUBBAND)                default 1 */
+    /* Per-subband detector only: the Gaussian kernel of Sec. 2.1.1 instead of the
+     * uniform box, truncated to the (2 box_r + 1)^2 window (box_r 1..16) and
+     * normalised per pixel by its weight over the in-image (and, when clipping,
+     * unflagged) window pixels.  C, S and the S/N are direct weighted FP32 window
+     * sums (rows, then columns) of the stored band image.                        */
+    int    kernel;        /* LPF_KERNEL_BOX / LPF_KERNEL_GAUSS                      default BOX */
+    float  gauss_sigma;   /* s in pixels (> 0, finite) for LPF_KERNEL_GAUSS          default 0   */
 } lpf_params;
 
 /* One candidate: pixel (y, x) of DM trial dm_idx (index into dm_grid) whose

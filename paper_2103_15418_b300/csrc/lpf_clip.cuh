@@ -1,13 +1,20 @@
 // Iterated sigma clipping of the per-subband detector (Sec. 2.1.1): at each
-// iteration the local centre C and spread S of a band image X are the box means
-// over the window pixels not yet flagged (normalised by their count n), and the
-// pixels with (X - C) / sqrt(S) > kappa join the flags; the loop stops when an
-// iteration flags nothing new (each launch of a later iteration then returns at
-// once) or after the iteration limit.  Candidates are the flagged pixels that
-// are (2k+1)^2 maxima of X (Sec. 2.1.2), with the S/N of the last iteration.
+// iteration the local centre C and spread S of a band image X are the
+// kernel-weighted means over the window pixels not yet flagged (normalised by
+// their kernel weight n), and the pixels with (X - C) / sqrt(S) > kappa join the
+// flags; the loop stops when an iteration flags nothing new (each launch of a
+// later iteration then returns at once) or after the iteration limit.
+// Candidates are the flagged pixels that are (2k+1)^2 maxima of X (Sec. 2.1.2),
+// with the S/N of the last iteration.
+//
+// The kernel on the (2r+1)^2 window is G(dy, dx) = w[|dy|] w[|dx|]: the uniform
+// box (w = 1) or the Gaussian exp(-(dy^2 + dx^2) / (2 s^2)), which factorises
+// into w[i] = exp(-i^2 / (2 s^2)).  With w = 1 every product below is exact, so
+// the box sums are plain FP32 sums.
 //
 // Planes [F][P] (FP32 unless noted): X, flags (u8), T1, T2 (row sums), C, n, S.
-// Box sums are direct FP32 sums over the clipped window, rows then columns.
+// Window sums are direct weighted FP32 sums over the clipped window, rows then
+// columns.
 #pragma once
 #include "lpf_kernels.cuh"
 
@@ -18,6 +25,7 @@ struct ClipArgs {
     uint8_t* flags;
     float *T1, *T2, *C, *N, *S;
     unsigned* changed;     // [iters]: bit set when iteration i flagged a new pixel
+    const float* w;        // [r + 1] kernel factors w[|d|]
     int F, H, W, r;
     int64_t P;
     float kappa;
@@ -35,8 +43,8 @@ __global__ void k_clip_init(ClipArgs c, const TS* __restrict__ slot) {
     }
 }
 
-// pass 0: T1 = row sums of X m, T2 = row sums of m (m = unflagged);
-// pass 1: T1 = row sums of (X - C)^2 m
+// pass 0: T1 = weighted row sums of X m, T2 = of m (m = unflagged);
+// pass 1: T1 = weighted row sums of (X - C)^2 m
 template <int PASS>
 __global__ void k_clip_rows(ClipArgs c, int it) {
     if (!clip_active(c, it)) return;
@@ -49,12 +57,13 @@ __global__ void k_clip_rows(ClipArgs c, int it) {
         float s1 = 0.f, s2 = 0.f;
         for (int xx = max(x - c.r, 0); xx <= min(x + c.r, c.W - 1); ++xx) {
             if (c.flags[row + xx]) continue;
+            const float g = __ldg(c.w + abs(xx - x));
             if (PASS == 0) {
-                s1 += c.X[row + xx];
-                s2 += 1.f;
+                s1 = fmaf(g, c.X[row + xx], s1);
+                s2 += g;
             } else {
                 const float d = c.X[row + xx] - c.C[row + xx];
-                s1 = fmaf(d, d, s1);
+                s1 = fmaf(g * d, d, s1);
             }
         }
         c.T1[row + x] = s1;
@@ -62,8 +71,8 @@ __global__ void k_clip_rows(ClipArgs c, int it) {
     }
 }
 
-// pass 0: n = column sums of T2, C = column sums of T1 / n (0 where n = 0);
-// pass 1: S = column sums of T1 / n
+// pass 0: n = weighted column sums of T2, C = weighted column sums of T1 / n
+// (0 where n = 0); pass 1: S = weighted column sums of T1 / n
 template <int PASS>
 __global__ void k_clip_cols(ClipArgs c, int it) {
     if (!clip_active(c, it)) return;
@@ -75,8 +84,9 @@ __global__ void k_clip_cols(ClipArgs c, int it) {
         const int64_t base = (int64_t)f * c.P + x;
         float s1 = 0.f, s2 = 0.f;
         for (int yy = max(y - c.r, 0); yy <= min(y + c.r, c.H - 1); ++yy) {
-            s1 += c.T1[base + (int64_t)yy * c.W];
-            if (PASS == 0) s2 += c.T2[base + (int64_t)yy * c.W];
+            const float g = __ldg(c.w + abs(yy - y));
+            s1 = fmaf(g, c.T1[base + (int64_t)yy * c.W], s1);
+            if (PASS == 0) s2 = fmaf(g, c.T2[base + (int64_t)yy * c.W], s2);
         }
         const int64_t o = base + (int64_t)y * c.W;
         if (PASS == 0) {

@@ -125,7 +125,9 @@ struct lpf_stream {
     unsigned* qc_words = nullptr;    // [2] pixel flags, discard mask
     lpf::QcRecord* h_qc = nullptr;   // [slots] pinned
     lpf::QcRecord last_qc{};
-    // iterated clipping of the per-subband detector (clip_iters > 1)
+    // clipping path of the per-subband detector (clip_iters > 1 or the Gaussian kernel)
+    bool clip = false;
+    float* clip_w = nullptr;         // [box_r + 1] kernel factors g(|d|) (1 for the box)
     uint8_t* clip_flags = nullptr;   // [F][P]
     float* clip_planes = nullptr;    // T1, T2, C, N, S: 5 x [F][P]
     unsigned* clip_changed = nullptr;  // [clip_iters]
@@ -213,6 +215,7 @@ void free_all(lpf_stream* s) {
             if (e) cudaEventDestroy(e);
     if (s->h_count) cudaFreeHost(s->h_count);
     if (s->h_qc) cudaFreeHost(s->h_qc);
+    if (s->clip_w) cudaFree(s->clip_w);
     if (s->clip_flags) cudaFree(s->clip_flags);
     if (s->clip_planes) cudaFree(s->clip_planes);
     if (s->clip_changed) cudaFree(s->clip_changed);
@@ -547,7 +550,7 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
             default: launch_ingest<__nv_bfloat16>(s, frame_dev, ring_slot); break;
         }
     };
-    const bool clip = s->prm.clip_iters > 1;
+    const bool clip = s->clip;
     // Residual path: the residuals and their shift-sum come from the pushed frame
     // and the residual ring, so the raw ring write of this frame waits until after
     // the shift-sum; by then the previous push's 3x3 pass (tail stream), which may
@@ -581,6 +584,7 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
         ca.N = ca.C + n;
         ca.S = ca.N + n;
         ca.changed = s->clip_changed;
+        ca.w = s->clip_w;
         ca.F = s->F; ca.H = s->H; ca.W = s->W; ca.r = s->prm.box_r; ca.P = s->P; ca.kappa = s->prm.kappa;
         const int g = 148 * 8;
         lpf::k_zero_u32<<<1, 32, 0, s->st>>>(s->clip_changed, s->prm.clip_iters);
@@ -738,6 +742,8 @@ void lpf_default_params(lpf_params* p) {
     p->qc_min_frames = 128;
     p->mode = LPF_MODE_DISPERSED;
     p->clip_iters = 1;
+    p->kernel = LPF_KERNEL_BOX;
+    p->gauss_sigma = 0.f;
 }
 
 const char* lpf_strerror(int code) {
@@ -778,8 +784,12 @@ int plan_stream(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, 
     if (H > (1 << 16) || W > (1 << 16) || buffer_depth > 32767 || F > 32) return LPF_E_ARG;
     if (!(prm.cadence_s > 0) || prm.box_r < 1 || prm.box_r > 16) return LPF_E_ARG;
     if (band ? (prm.lmax_r < 1 || prm.lmax_r > 3) : prm.lmax_r != 1) return LPF_E_ARG;
-    // the per-subband detector runs on the residual planes: streaming filter only
-    if (band && (prm.filter_impl == 1 || (prm.box_r != 7 && prm.box_r != 15))) return LPF_E_ARG;
+    // the Gaussian kernel: per-subband detector, on the clipping path (any box_r)
+    if (prm.kernel != LPF_KERNEL_BOX && prm.kernel != LPF_KERNEL_GAUSS) return LPF_E_ARG;
+    const bool gauss = prm.kernel == LPF_KERNEL_GAUSS;
+    if (gauss && (!band || !(prm.gauss_sigma > 0) || !std::isfinite(prm.gauss_sigma))) return LPF_E_ARG;
+    // the per-subband detector with the box runs on the residual planes: streaming filter only
+    if (band && !gauss && (prm.filter_impl == 1 || (prm.box_r != 7 && prm.box_r != 15))) return LPF_E_ARG;
     // iterated clipping: per-subband detector only (the dispersed search is one pass)
     if (prm.clip_iters < 1 || prm.clip_iters > 16 || (!band && prm.clip_iters != 1)) return LPF_E_ARG;
     if (prm.dtype < LPF_FP32 || prm.dtype > LPF_BF16 || prm.cand_cap < 1 || prm.dyn_box_r < 0) return LPF_E_ARG;
@@ -825,7 +835,11 @@ int plan_stream(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, 
     s->tiles_y = (H + lpf::kTile - 1) / lpf::kTile;
     s->filter_rmax = prm.box_r <= 8 ? 8 : 16;
     s->filter_smem = filter_smem_bytes(prm.box_r, s->filter_rmax);
-    s->stream_filter = band || prm.filter_impl == 2 || (prm.filter_impl == 0 && (prm.box_r == 7 || prm.box_r == 15));
+    // the clipping path (per-subband detector, clip_iters > 1 or the Gaussian kernel)
+    // sums its windows directly from the raw ring: no residual ring, no crossing list
+    s->clip = band && (prm.clip_iters > 1 || gauss);
+    s->stream_filter = !s->clip && (band || prm.filter_impl == 2 ||
+                                    (prm.filter_impl == 0 && (prm.box_r == 7 || prm.box_r == 15)));
     s->n_strips = (W + lpf::kStreamTX - 1) / lpf::kStreamTX;
     // the per-subband detector has only F rows: split each strip into row segments
     // so that about two waves of 4 CTAs per SM run (each segment after the first
@@ -854,8 +868,9 @@ size_t footprint_bytes(const lpf_stream* s) {
     size_t t = (size_t)s->depth * s->F * s->P * s->elem * (s->stream_filter ? 2 : 1);
     t += b(nd * s->P * 4) + b(2 * (size_t)s->F * s->HW * 4) + b(nd * s->F * 2) + b(nd * 4);
     if (s->xcap > 0) t += b((size_t)s->xcap * 8) + b((size_t)s->xcap * 4);
-    if (s->prm.clip_iters > 1)
-        t += b((size_t)s->F * s->P) + b(5 * (size_t)s->F * s->P * 4) + b((size_t)s->prm.clip_iters * 4);
+    if (s->clip)
+        t += b((size_t)s->F * s->P) + b(5 * (size_t)s->F * s->P * 4) + b((size_t)s->prm.clip_iters * 4) +
+             b((size_t)(s->prm.box_r + 1) * 4);
     if (s->prm.qc) {
         t += 2 * b((size_t)s->F * s->P * 4) + b((size_t)s->F * 4) + b((size_t)s->F * 4) +
              b((size_t)s->F * lpf::kQcScanBlocks * 8) + b(2 * 4);
@@ -961,7 +976,16 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
         if (rc == LPF_OK && cudaEventCreateWithFlags(&s->slots[i].done, cudaEventDisableTiming) != cudaSuccess)
             rc = LPF_E_CUDA;
     }
-    if (prm.clip_iters > 1) {
+    if (s->clip) {
+        // g(i) = exp(-i^2 / (2 s^2)) in FP64, stored as FP32 (1 for the box)
+        std::vector<float> g(prm.box_r + 1, 1.0f);
+        if (prm.kernel == LPF_KERNEL_GAUSS)
+            for (int i = 0; i <= prm.box_r; ++i)
+                g[i] = (float)std::exp(-(double)i * i / (2.0 * (double)prm.gauss_sigma * prm.gauss_sigma));
+        if (rc == LPF_OK) rc = dev_alloc(s, &s->clip_w, g.size());
+        if (rc == LPF_OK && cudaMemcpy(s->clip_w, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice) !=
+                                cudaSuccess)
+            rc = LPF_E_CUDA;
         if (rc == LPF_OK) rc = dev_alloc(s, &s->clip_flags, (size_t)F * s->P);
         if (rc == LPF_OK) rc = dev_alloc(s, &s->clip_planes, 5 * (size_t)F * s->P);
         if (rc == LPF_OK) rc = dev_alloc(s, &s->clip_changed, (size_t)prm.clip_iters);

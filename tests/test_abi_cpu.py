@@ -39,6 +39,7 @@ def test_struct_layouts():
     # the fields after the pointer read back the library's defaults: same layout
     assert (p.filter_impl, p.qc, p.qc_z, p.qc_zeta, p.qc_min_frames, p.mode, p.clip_iters) == \
         (0, 0, 5.0, 20.0, 128, 0, 1)
+    assert (p.kernel, p.gauss_sigma) == (0, 0.0)
 
 
 def test_strerror_names_every_code():
@@ -68,6 +69,12 @@ def test_argument_validation_before_any_cuda_call():
         dict(H=8, W=8, freqs_mhz=f, dm_grid=None, depth=2, mode="subband", filter_impl="tiled"),
         dict(H=8, W=8, freqs_mhz=f, dm_grid=dm, depth=8, clip_iters=3),        # one pass for DM trials
         dict(H=8, W=8, freqs_mhz=f, dm_grid=None, depth=2, mode="subband", clip_iters=17),
+        dict(H=8, W=8, freqs_mhz=f, dm_grid=dm, depth=8, kernel="gauss", gauss_sigma=2.0),  # subband only
+        dict(H=8, W=8, freqs_mhz=f, dm_grid=None, depth=2, mode="subband", kernel="gauss"),  # s = 0
+        dict(H=8, W=8, freqs_mhz=f, dm_grid=None, depth=2, mode="subband", kernel="gauss",
+             gauss_sigma=float("inf")),
+        dict(H=8, W=8, freqs_mhz=f, dm_grid=None, depth=2, mode="subband", kernel="gauss",
+             gauss_sigma=2.0, box_r=17),
     ]
     for kw in bad:
         with pytest.raises(lpf.LpfError) as e:
@@ -145,10 +152,18 @@ def test_subband_detector_footprint():
 
 
 def test_clipping_footprint():
-    """Iterated clipping adds a flag plane and five FP32 planes per band."""
+    """The clipping path (iterations, or the Gaussian kernel) adds a flag plane and
+    five FP32 planes per band and drops the residual ring (depth 2, FP32) and the
+    crossing list (max(cand_cap, F H W / 32) keys and S/N values)."""
     import synth
     sp = synth.spec_aartfaac(H=256, W=256)
     one = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, None, 2, mode="subband", lmax_r=3)
     many = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, None, 2, mode="subband", lmax_r=3, clip_iters=4)
+    gauss = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, None, 2, mode="subband", lmax_r=3, kernel="gauss",
+                          gauss_sigma=4.0, box_r=9)
     px = sp.F * sp.H * sp.W
-    assert px * 21 <= many - one < px * 21 + 4096
+    xcap = max(1 << 20, px // 32)
+    delta = px * 21 - 2 * px * 4 - xcap * 12
+    # (+ the kernel factors and the statistics partials of the other block layout)
+    assert delta <= many - one < delta + 65536
+    assert delta <= gauss - one < delta + 65536

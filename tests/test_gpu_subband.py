@@ -123,3 +123,32 @@ def test_subband_clipping_matches_oracle(lib, dtype):
                 assert abs(gstats[b][0] - mean) <= 1e-4 * abs(mean) + 1e-6, (b, gstats[b], mean)
                 assert abs(gstats[b][1] - rms) <= 1e-4 * abs(rms) + 1e-6, (b, gstats[b], rms)
     assert more > 0          # clipping found sources the one-pass filter missed
+
+
+@pytest.mark.parametrize("dtype,iters", [("fp32", 1), ("fp32", 3), ("fp16", 1), ("bf16", 3)])
+def test_subband_gaussian_kernel_matches_oracle(lib, dtype, iters):
+    """The per-subband detector with the Gaussian background kernel of Sec. 2.1.1
+    (s = 3 px on the 19x19 window), one pass and three clipping iterations,
+    against clip_detect(..., s): candidates, S/N and per-band statistics."""
+    spec = synth.spec_aartfaac(H=96, W=128, n_sources=0, n_pulses=0, box_r=9, n_frames=6)
+    st = synth.SyntheticStream(spec, seed=37)
+    s_px, k, matched = 3.0, 3, 0
+    with lib.Stream(spec.H, spec.W, spec.freqs_mhz, None, 1, kappa=spec.kappa, box_r=spec.box_r, dtype=dtype,
+                    mode="subband", lmax_r=k, clip_iters=iters, kernel="gauss", gauss_sigma=s_px) as s:
+        for T in range(3):
+            frame = clip_frame(spec, st, T)
+            s.push(torch.from_numpy(frame).cuda(), T)
+            _, c, n, trunc = s.poll(timeout_ms=60000)
+            assert not trunc and n == len(c) and np.all(c["t0"] == T)
+            assert_sorted_unique(c)
+            x = O.storage_round(frame, dtype)
+            gstats = s.stats()
+            for b in range(spec.F):
+                m = O.clip_detect(x[b], spec.box_r, spec.kappa, k, iters, s=s_px)
+                m["abs_sum"] = np.abs(x[b])
+                nm, _, _ = compare_trial(c[c["dm_idx"] == b], m, 1, spec.kappa)
+                matched += nm
+                mean, rms, _ = O.frame_stats(m["snr"], m["valid"])
+                assert abs(gstats[b][0] - mean) <= 1e-4 * abs(mean) + 1e-6, (b, gstats[b], mean)
+                assert abs(gstats[b][1] - rms) <= 1e-4 * abs(rms) + 1e-6, (b, gstats[b], rms)
+    assert matched > 3 * spec.F
