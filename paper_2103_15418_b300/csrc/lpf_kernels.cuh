@@ -57,6 +57,22 @@ __device__ __forceinline__ void st4(__nv_bfloat16* p, float4 v) {
 __device__ __forceinline__ void st1(float* p, float v) { *p = v; }
 __device__ __forceinline__ void st1(__half* p, float v) { *p = __float2half_rn(v); }
 __device__ __forceinline__ void st1(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+// True when no pixel of the (2k+1)^2 window around (y, x), clipped to the H x W
+// image, exceeds v (ties count as maxima, Sec. 2.1.2), reading pixels through
+// ld(yy, xx).  The 3x3 ring is tested first: a pixel of a bright region that is
+// not its peak usually has a larger neighbour there.
+template <typename Ld>
+__device__ __forceinline__ bool window_is_max(int y, int x, int k, int H, int W, float v, Ld&& ld) {
+    const int k1 = k < 1 ? k : 1;
+    for (int yy = max(y - k1, 0); yy <= min(y + k1, H - 1); ++yy)
+        for (int xx = max(x - k1, 0); xx <= min(x + k1, W - 1); ++xx)
+            if (ld(yy, xx) > v) return false;
+    for (int yy = max(y - k, 0); yy <= min(y + k, H - 1); ++yy)
+        for (int xx = max(x - k, 0); xx <= min(x + k, W - 1); ++xx)
+            if ((yy - y > 1 || y - yy > 1 || xx - x > 1 || x - xx > 1) && ld(yy, xx) > v) return false;
+    return true;
+}
+
 // v as the storage type TS holds it (round to nearest even, as st1 and st4 store)
 template <typename TS> __device__ __forceinline__ float as_stored(float v);
 template <> __device__ __forceinline__ float as_stored<float>(float v) { return v; }

@@ -207,11 +207,8 @@ __device__ __forceinline__ bool band_is_max(const ResArgs& ra, int row, int ys, 
     const FilterArgs& a = ra.a;
     const TS* plane = static_cast<const TS*>(ra.ring) + ((int64_t)ra.Tmod * ra.F + row) * a.P;
     const float c = ld1(plane + (int64_t)ys * a.W + xs);
-    const int k = ra.band_k;
-    for (int yy = max(ys - k, 0); yy <= min(ys + k, a.H - 1); ++yy)
-        for (int xx = max(xs - k, 0); xx <= min(xs + k, a.W - 1); ++xx)
-            if (ld1(plane + (int64_t)yy * a.W + xx) > c) return false;
-    return true;
+    return window_is_max(ys, xs, ra.band_k, a.H, a.W, c,
+                         [&](int yy, int xx) { return ld1(plane + (int64_t)yy * a.W + xx); });
 }
 
 // Candidates of one image row of a warp (lanes with cand set): the 3x3 local

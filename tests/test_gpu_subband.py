@@ -125,12 +125,17 @@ def test_subband_clipping_matches_oracle(lib, dtype):
     assert more > 0          # clipping found sources the one-pass filter missed
 
 
-@pytest.mark.parametrize("dtype,iters", [("fp32", 1), ("fp32", 3), ("fp16", 1), ("bf16", 3)])
-def test_subband_gaussian_kernel_matches_oracle(lib, dtype, iters):
+@pytest.mark.parametrize("dtype,iters,r,H,W", [("fp32", 1, 9, 96, 128), ("fp32", 3, 15, 96, 128),
+                                               ("fp16", 1, 15, 96, 128), ("bf16", 3, 7, 96, 128),
+                                               ("fp32", 2, 7, 97, 531), ("fp32", 2, 15, 45, 70)])
+def test_subband_gaussian_kernel_matches_oracle(lib, dtype, iters, r, H, W):
     """The per-subband detector with the Gaussian background kernel of Sec. 2.1.1
-    (s = 3 px on the 19x19 window), one pass and three clipping iterations,
-    against clip_detect(..., s): candidates, S/N and per-band statistics."""
-    spec = synth.spec_aartfaac(H=96, W=128, n_sources=0, n_pulses=0, box_r=9, n_frames=6)
+    (s = 3 px on the (2r+1)^2 window: r = 7 and 15 take the tiled window sums, 9
+    the direct ones), one pass and clipping iterations, against
+    clip_detect(..., s): candidates, S/N and per-band statistics; ragged sizes
+    (a second 512-column segment, partial 32 x 64 tiles, windows wider than the
+    image) included."""
+    spec = synth.spec_aartfaac(H=H, W=W, n_sources=0, n_pulses=0, box_r=r, n_frames=6)
     st = synth.SyntheticStream(spec, seed=37)
     s_px, k, matched = 3.0, 3, 0
     with lib.Stream(spec.H, spec.W, spec.freqs_mhz, None, 1, kappa=spec.kappa, box_r=spec.box_r, dtype=dtype,
@@ -151,4 +156,4 @@ def test_subband_gaussian_kernel_matches_oracle(lib, dtype, iters):
                 mean, rms, _ = O.frame_stats(m["snr"], m["valid"])
                 assert abs(gstats[b][0] - mean) <= 1e-4 * abs(mean) + 1e-6, (b, gstats[b], mean)
                 assert abs(gstats[b][1] - rms) <= 1e-4 * abs(rms) + 1e-6, (b, gstats[b], rms)
-    assert matched > 3 * spec.F
+    assert matched > 2 * spec.F
