@@ -52,7 +52,7 @@ def parse():
                          "31x31 window (0 = the uniform box)")
     ap.add_argument("--qc", action="store_true",
                     help="quality control of every frame before the search (band and pixel scores)")
-    ap.add_argument("--workload", default="aartfaac", choices=["aartfaac", "serving", "subband"],
+    ap.add_argument("--workload", default="aartfaac", choices=["aartfaac", "serving", "subband", "stress"],
                     help="serving: four concurrent FP16 streams through the C++ serving loop")
     ap.add_argument("--cadence", type=float, default=1.0, help="serving: frame cadence in seconds")
     ap.add_argument("--frames", type=int, default=60, help="serving: frames per stream")
@@ -514,8 +514,74 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def run_stress(args):
+    """Stress workload: 2048^2 px, 32 subbands (57.6-63.85 MHz), 1001 DM trials, FP16
+    ring of depth 114 (the DM 500 sweep spans 113 frames).  Each step pushes a frame,
+    polls the oldest unpolled one and gathers the 32 x 64 FP32 dynamic spectra of its
+    candidates; frames per second against the 1 s cadence is the real-time factor."""
+    import torch
+    import paper_2103_15418_b300 as lpf
+    spec = synth.spec_stress(depth=114)
+    st = synth.SyntheticStream(spec, seed=50)
+    npool = 4
+    pool = [torch.from_numpy(st.frame(t)).cuda() for t in range(npool)]
+    cur = torch.cuda.Stream()               # the search stream (the timing events are recorded on it)
+    s = lpf.Stream(spec.H, spec.W, spec.freqs_mhz, spec.dm_grid, spec.depth, kappa=spec.kappa,
+                   box_r=spec.box_r, dtype="fp16", result_slots=RESULT_SLOTS, cuda_stream=cur)
+    info = s.info()
+    Tw, T = 64, 0
+    ncand, nds = [], []
+
+    def poll_and_gather():
+        Tp, c, n, _ = s.poll(timeout_ms=600000)
+        g = 0
+        if len(c) and Tp >= Tw - 1:         # once Tw frames exist
+            s.dynspec(c, Tw, sync=False)    # [n, 32, 64] FP32 on the search stream
+            g = len(c)
+        ncand.append(n)
+        nds.append(g)
+
+    for _ in range(spec.depth + args.warmup):
+        s.push(pool[T % npool], T)
+        T += 1
+        poll_and_gather()
+    ahead = max(1, RESULT_SLOTS - 1)
+    s.set_profiling(True)
+    s.kernel_times(reset=True)
+    torch.cuda.synchronize()
+    ncand.clear()
+    nds.clear()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(cur)
+    for k in range(args.steps):
+        s.push(pool[T % npool], T)
+        T += 1
+        if k >= ahead:
+            poll_and_gather()
+    for _ in range(ahead):
+        poll_and_gather()
+    ev1.record(cur)
+    torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    kt = s.kernel_times(reset=True)
+    s.close()
+    per_push = {n: kt[n][0] / max(kt[n][1], 1) for n in kt}
+    fps = args.steps / elapsed
+    print(json.dumps({
+        "metric": METRIC, "value": spec.H * spec.W * spec.n_dm * fps, "unit": METRIC,
+        "workload": "stress-2048x2048-32sb-1001dm-depth114-fp16-dynspec32x64", "steps": args.steps,
+        "ms_per_step": 1e3 * elapsed / args.steps, "frames_per_s": fps, "real_time_factor": fps * spec.cadence_s,
+        "n_distinct": info["n_distinct"], "max_delay": info["max_delay"],
+        "device_bytes": info.get("device_bytes"), "kernel_ms_per_step": per_push,
+        "candidates_per_step": float(np.mean(ncand)), "dynspec_records_per_step": float(np.mean(nds)),
+        "data": "synthetic (seeded: noise, gradient, 200 dispersed pulses, 1% RFI stripes)"}), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "stress":
+        run_stress(args)
+        return
     if args.workload == "serving":
         run_serving(args)
         return

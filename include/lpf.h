@@ -203,6 +203,9 @@ int lpf_poll_candidates(lpf_stream* s, lpf_candidate* out_host, int cap, int* n_
  * [n][F][Tw]) receives out[i][f][tau] = X_f(T - Tw + 1 + tau) at (y_i, x_i), or
  * the maximum over the (2 dyn_box_r + 1)^2 box clipped to the image.  Enqueued
  * on the stream; out_dev is valid once the stream reaches it (lpf_stream_sync).
+ * The coordinates are staged in page-locked memory the stream owns, so c_host
+ * may be reused when the call returns; the call waits only for the previous
+ * call's coordinate copy.
  * Errors: LPF_E_ARG (pixel outside the image, n < 0, Tw < 1), LPF_E_DEPTH (Tw >
  * buffer_depth), LPF_E_STALE (a needed frame was overwritten or precedes the
  * first push), LPF_E_NODATA (nothing polled yet).

@@ -241,8 +241,12 @@ class Stream:
         k = min(n.value, cap, self._cap)
         return T.value, buf[:k].copy(), n.value, rc == LPF_E_TRUNCATED
 
-    def dynspec(self, cands, Tw: int, out=None):
-        """FP32 CUDA tensor [n, F, Tw] of the candidates' dynamic spectra (last polled frame)."""
+    def dynspec(self, cands, Tw: int, out=None, sync: bool = True):
+        """FP32 CUDA tensor [n, F, Tw] of the candidates' dynamic spectra (last polled frame).
+        The gather is enqueued on the stream's CUDA stream; sync=True waits for the
+        stream, so the tensor may be read from any torch stream.  sync=False leaves it
+        to the caller (work that follows on the CUDA stream given at construction is
+        ordered after the gather)."""
         import torch
         c = np.ascontiguousarray(cands, dtype=CANDIDATE_DTYPE)
         n = len(c)
@@ -251,6 +255,8 @@ class Stream:
         _check(load().lpf_extract_dynspec(self._h, c_void_p(c.ctypes.data) if n else None, n, int(Tw),
                                           c_void_p(out.data_ptr()) if n else None),
                "lpf_extract_dynspec")
+        if sync:
+            self.sync()
         return out
 
     # ---------------------------------------------------------------- queries

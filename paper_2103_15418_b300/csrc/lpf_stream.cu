@@ -111,6 +111,9 @@ struct lpf_stream {
     cudaStream_t tail_st = nullptr;  // ordering, formatting, statistics, result copies
     int2* d_yx = nullptr;
     int yx_cap = 0;
+    int2* h_yx = nullptr;           // page-locked staging of the dynspec coordinates
+    int h_yx_cap = 0;
+    cudaEvent_t yx_copied = nullptr; // the last staging copy has been read
     size_t device_bytes = 0;
 
     // host pinned
@@ -214,6 +217,8 @@ void free_all(lpf_stream* s) {
         for (auto& e : row)
             if (e) cudaEventDestroy(e);
     if (s->h_count) cudaFreeHost(s->h_count);
+    if (s->h_yx) cudaFreeHost(s->h_yx);
+    if (s->yx_copied) cudaEventDestroy(s->yx_copied);
     if (s->h_qc) cudaFreeHost(s->h_qc);
     if (s->clip_w) cudaFree(s->clip_w);
     if (s->clip_flags) cudaFree(s->clip_flags);
@@ -444,8 +449,10 @@ int set_res_attributes() {
 // split into two segments (each restarts its register state) for parallelism.
 template <typename TS>
 void launch_dedisperse_ring(lpf_stream* s, const void* ring_v, float* out, int n_rows, int Tmod) {
-    // two row segments (more where one segment's plane table would exceed 48 KB of shared memory)
-    int nseg = n_rows >= 32 ? 2 : 1;
+    // two row segments for FP32 rings, three for 16-bit rings (whose threads own 8
+    // pixels, so half as many CTAs per segment); more where one segment's plane
+    // table would exceed 48 KB of shared memory
+    int nseg = n_rows >= 32 ? (sizeof(TS) == 4 ? 2 : 3) : 1;
     while (lpf::dedisperse_smem_bytes((n_rows + nseg - 1) / nseg, s->F) > 48 * 1024) ++nseg;
     const int seg = (n_rows + nseg - 1) / nseg;
     const size_t smem = lpf::dedisperse_smem_bytes(seg, s->F);
@@ -1159,12 +1166,26 @@ int lpf_extract_dynspec(lpf_stream* s, const lpf_candidate* c_host, int n, int T
     if (T - Tw + 1 < s->T_first) return LPF_E_STALE;
     if (s->last_T - s->depth + 1 > T - Tw + 1) return LPF_E_STALE;
     if (n == 0) return LPF_OK;
-    std::vector<int2> yx(n);
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < n; ++i)
         if (c_host[i].y < 0 || c_host[i].y >= s->H || c_host[i].x < 0 || c_host[i].x >= s->W) return LPF_E_ARG;
-        yx[i] = make_int2(c_host[i].y, c_host[i].x);
-    }
     if (cudaSetDevice(s->dev) != cudaSuccess) return LPF_E_CUDA;
+    // coordinates staged in page-locked memory, so the copy and the gather stay
+    // asynchronous; the staging buffer is refilled once the previous copy has read it
+    if (!s->yx_copied && cudaEventCreateWithFlags(&s->yx_copied, cudaEventDisableTiming) != cudaSuccess)
+        return LPF_E_CUDA;
+    LPF_TRY(cudaEventSynchronize(s->yx_copied));
+    if (n > s->h_yx_cap) {
+        if (s->h_yx) cudaFreeHost(s->h_yx);
+        s->h_yx = nullptr;
+        s->h_yx_cap = 0;
+        if (cudaMallocHost((void**)&s->h_yx, (size_t)n * sizeof(int2)) != cudaSuccess) {
+            cudaGetLastError();
+            s->h_yx = nullptr;
+            return LPF_E_OOM;
+        }
+        s->h_yx_cap = n;
+    }
+    for (int i = 0; i < n; ++i) s->h_yx[i] = make_int2(c_host[i].y, c_host[i].x);
     if (n > s->yx_cap) {
         LPF_TRY(cudaStreamSynchronize(s->st));
         if (s->d_yx) { cudaFree(s->d_yx); s->device_bytes -= (size_t)s->yx_cap * sizeof(int2); }
@@ -1174,7 +1195,8 @@ int lpf_extract_dynspec(lpf_stream* s, const lpf_candidate* c_host, int n, int T
         if (rc != LPF_OK) return rc;
         s->yx_cap = n;
     }
-    LPF_TRY(cudaMemcpyAsync(s->d_yx, yx.data(), (size_t)n * sizeof(int2), cudaMemcpyHostToDevice, s->st));
+    LPF_TRY(cudaMemcpyAsync(s->d_yx, s->h_yx, (size_t)n * sizeof(int2), cudaMemcpyHostToDevice, s->st));
+    LPF_TRY(cudaEventRecord(s->yx_copied, s->st));
     int slot_first = (int)((T - Tw + 1) % s->depth);
     cudaGetLastError();
     switch (s->prm.dtype) {
@@ -1183,8 +1205,6 @@ int lpf_extract_dynspec(lpf_stream* s, const lpf_candidate* c_host, int n, int T
         default: launch_dynspec<__nv_bfloat16>(s, n, Tw, slot_first, out_dev); break;
     }
     if (cudaGetLastError() != cudaSuccess) return LPF_E_CUDA;
-    // the pageable coordinate vector must outlive the copy
-    LPF_TRY(cudaStreamSynchronize(s->st));
     return LPF_OK;
 }
 

@@ -79,6 +79,31 @@ def test_ragged_sizes_and_small_box(lib, r):
             compare_push(c, fa, T, delays, spec.box_r, spec.kappa, gpu_stats=s.stats())
 
 
+@pytest.mark.parametrize("F,dtype", [(32, "fp32"), (32, "fp16"), (24, "bf16"), (17, "fp32")])
+def test_more_than_16_subbands(lib, F, dtype):
+    """More than 16 subbands (the shift-sum with 8 bytes of each plane per thread;
+    24 and 17 take the instantiation for F below its maximum), FP32 and 16-bit
+    rings, a 66 x 90 image (rows not a multiple of 4 pixels)."""
+    spec = synth.spec_tiny(H=66, W=90, freqs_mhz=synth.subband_centres([57.6], F),
+                           dm_grid=np.arange(0, 40, 2.0), depth=24, box_r=7, kappa=4.0, n_sources=4)
+    st = synth.SyntheticStream(spec, seed=13)
+    fa = cached_frames(st, dtype)
+    ra = None if dtype == "fp32" else cached_residuals(st, dtype, spec.box_r)
+    delays = O.delay_table(spec.freqs_mhz, spec.dm_grid, spec.cadence_s)
+    assert delays.max() + 1 <= spec.depth
+    matched = 0
+    with _open(lib, spec, dtype=dtype) as s:
+        for T in range(int(delays.max()) + 6):
+            _push(s, st, T)
+            _, c, n, trunc = s.poll(timeout_ms=60000)
+            assert not trunc
+            if T >= delays.max():
+                assert_sorted_unique(c)
+                res = compare_push(c, fa, T, delays, spec.box_r, spec.kappa, gpu_stats=s.stats(), res_at=ra)
+                matched += res["matched"]
+    assert matched > 0
+
+
 @pytest.mark.parametrize("r", [1, 8, 16])
 def test_box_radius_extremes(lib, r):
     spec = synth.spec_tiny(H=80, W=72, box_r=r, kappa=4.0, n_frames=8)
