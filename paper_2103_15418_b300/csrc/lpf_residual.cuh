@@ -142,40 +142,11 @@ struct ResArgs {
 // a crossing slot reserved by a warp that resolved its crossings itself
 constexpr uint64_t kNoCrossing = ~0ull;
 
-// D = sum_f X_f(t_f) of a delay row on the 3x3 window around (ys, xs), summed
-// from the raw ring in the order f = 0 .. F-1 in FP32 (the arithmetic of the
-// shift-sum, so the same values); -inf outside the image.
-template <typename TS>
-__device__ __forceinline__ void d_window3(const ResArgs& ra, int row, int ys, int xs, float nb[9]) {
-    const FilterArgs& a = ra.a;
-    const int H = a.H, W = a.W;
-    const TS* ring = static_cast<const TS*>(ra.ring);
-    const int16_t* lr = ra.lag + (int64_t)row * ra.F;
-    int64_t off[9];
-    bool in[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const int yy = ys + k / 3 - 1, xx = xs + k % 3 - 1;
-        in[k] = yy >= 0 && yy < H && xx >= 0 && xx < W;
-        off[k] = in[k] ? (int64_t)yy * W + xx : 0;
-    }
-    for (int f = 0; f < ra.F; ++f) {
-        int slot = ra.Tmod - (int)__ldg(lr + f);
-        if (slot < 0) slot += ra.depth;
-        const TS* plane = ring + ((int64_t)slot * ra.F + f) * a.P;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const float v = in[k] ? ld1(plane + off[k]) : 0.f;
-            nb[k] = (f == 0) ? v : nb[k] + v;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 9; ++k)
-        if (!in[k]) nb[k] = -INFINITY;
-}
-
-// The same values one window pixel at a time (few registers: the in-kernel
-// resolution of an overflowing crossing list).
+// D = sum_f X_f(t_f) of a delay row at a pixel is summed from the raw ring in
+// the order f = 0 .. F-1 in FP32 (the arithmetic of the shift-sum, so the same
+// values); -inf outside the image.  d_window3_lean: the 3x3 window one pixel at
+// a time (few registers: the in-kernel resolution of an overflowing crossing
+// list).
 template <typename TS>
 __device__ __forceinline__ void d_window3_lean(const ResArgs& ra, int row, int ys, int xs, float nb[9]) {
     const FilterArgs& a = ra.a;
@@ -197,6 +168,53 @@ __device__ __forceinline__ void d_window3_lean(const ResArgs& ra, int row, int y
         }
         nb[k] = v;
     }
+}
+
+// Sums D = sum_f X_f(t_f) (FP32, f = 0 .. F-1, as the shift-sum) at the NK
+// pixels (ys + dy[k], xs + dx[k]) from the raw ring; -inf outside the image.
+template <typename TS, int NK>
+__device__ __forceinline__ void d_points(const ResArgs& ra, int row, int ys, int xs, const int (&dy)[NK],
+                                         const int (&dx)[NK], float (&v)[NK]) {
+    const FilterArgs& a = ra.a;
+    const TS* ring = static_cast<const TS*>(ra.ring);
+    const int16_t* lr = ra.lag + (int64_t)row * ra.F;
+    int64_t off[NK];
+    bool in[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        const int yy = ys + dy[k], xx = xs + dx[k];
+        in[k] = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+        off[k] = in[k] ? (int64_t)yy * a.W + xx : 0;
+    }
+    for (int f = 0; f < ra.F; ++f) {
+        int slot = ra.Tmod - (int)__ldg(lr + f);
+        if (slot < 0) slot += ra.depth;
+        const TS* plane = ring + ((int64_t)slot * ra.F + f) * a.P;
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            const float x = in[k] ? ld1(plane + off[k]) : 0.f;
+            v[k] = (f == 0) ? x : v[k] + x;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NK; ++k)
+        if (!in[k]) v[k] = -INFINITY;
+}
+
+// Whether D(ys, xs) is the maximum of its 3x3 window clipped to the image (ties
+// count), with the same D values as d_window3: the centre and its four edge
+// neighbours first, the four diagonal ones only if none of those is larger
+// (most crossings of a source's clump have a larger edge neighbour).
+template <typename TS>
+__device__ __forceinline__ bool d_is_max3(const ResArgs& ra, int row, int ys, int xs) {
+    constexpr int ey[5] = {0, -1, 1, 0, 0}, ex[5] = {0, 0, 0, -1, 1};
+    float v[5];
+    d_points<TS, 5>(ra, row, ys, xs, ey, ex, v);
+    if (v[1] > v[0] || v[2] > v[0] || v[3] > v[0] || v[4] > v[0]) return false;
+    constexpr int gy[4] = {-1, -1, 1, 1}, gx[4] = {-1, 1, -1, 1};
+    float g[4];
+    d_points<TS, 4>(ra, row, ys, xs, gy, gx, g);
+    return !(g[0] > v[0] || g[1] > v[0] || g[2] > v[0] || g[3] > v[0]);
 }
 
 // Per-subband detector: whether X_f(y, x) of the newest frame (ring slot Tmod,
@@ -560,12 +578,7 @@ __global__ void __launch_bounds__(256) k_lmax_res(ResArgs ra) {
                 if constexpr (BAND) {
                     cand = band_is_max<TS>(ra, row, ys, xs);
                 } else {
-                    float nb[9];
-                    d_window3<TS>(ra, row, ys, xs, nb);
-                    cand = true;
-#pragma unroll
-                    for (int k = 0; k < 9; ++k)
-                        if (k != 4 && nb[k] > nb[4]) cand = false;
+                    cand = d_is_max3<TS>(ra, row, ys, xs);
                 }
             }
         }
