@@ -10,6 +10,7 @@
 #include "lpf_kernels.cuh"
 #include "lpf_dedisperse.cuh"
 #include "lpf_residual.cuh"
+#include "lpf_filter_res.cuh"
 #include "lpf_qc.cuh"
 #include "lpf_clip.cuh"
 
