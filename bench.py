@@ -86,9 +86,10 @@ def workload_spec(dtype):
 FILTER_OPS_PER_PIXEL_TRIAL = 11
 
 
-def kernel_traffic():
-    """DRAM bytes per launch from the committed ncu capture, or None where the kernel's
-    source has changed since the counters were taken."""
+def kernel_traffic(field="dram_bytes_per_launch"):
+    """A per-launch counter (DRAM bytes, or executed warp instructions) from the
+    committed ncu capture, or None where the kernel's source has changed since the
+    counters were taken or the capture has no such counter."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -102,7 +103,7 @@ def kernel_traffic():
             sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
         except Exception:
             continue
-        out[k] = v["dram_bytes_per_launch"] if sha == v["sha256"] else None
+        out[k] = v.get(field) if sha == v["sha256"] else None
     return out
 
 
@@ -358,6 +359,16 @@ def run_ours(args):
               "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
               "traffic": traffic.get("k_filter_res"),
               "algorithmic_flop_per_launch": f_ops, "avg_launch_ms": f_ms, "launches_per_step": 1}
+    # the filter is bound by instruction issue: executed warp instructions per launch
+    # (ncu) over the event-timed launch, against 4 schedulers per SM at the clock
+    f_inst = kernel_traffic("warp_inst_per_launch").get("k_filter_res")
+    issue_peak = sms * 4 * sm_mhz * 1e6 / 1e12
+    roof_f_issue = {"kernel": "k_filter_res<15> (instruction issue)", "bound": "issue",
+                    "achieved": f_inst / (f_ms / 1e3) / 1e12 if f_inst else None, "peak": issue_peak,
+                    "unit": "T warp-instructions/s",
+                    "frac": f_inst / (f_ms / 1e3) / 1e12 / issue_peak if f_inst else None,
+                    "peak_source": f"{sms} SMs x 4 schedulers x {sm_mhz:.0f} MHz",
+                    "warp_instructions_per_launch": f_inst, "avg_launch_ms": f_ms}
     roof = roof_f if f_ms >= dd_ms else roof_dd
     # quality control + ingest (k_qc_scan, k_qc_decide, k_residual, k_ingest_qc): the
     # QC passes read the frame and the running mean and m2 twice and write them once
@@ -392,7 +403,7 @@ def run_ours(args):
         # 3 per sort pass, format, stats
         "gpu_launches": int(args.steps * (8 + 3 * _passes(spec) + (2 if args.qc else 0))),
         "roofline": roof,
-        "rooflines": [roof_f, roof_dd] + ([roof_qc] if args.qc else []),
+        "rooflines": [roof_f, roof_f_issue, roof_dd] + ([roof_qc] if args.qc else []),
         "path_roofline": {"bound": "hbm", "achieved": path_ach, "peak": hbm_peak, "unit": "GB/s",
                           "frac": path_ach / hbm_peak,
                           "algorithmic_bytes_per_step": nbytes["path"],
