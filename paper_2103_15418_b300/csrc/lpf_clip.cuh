@@ -14,9 +14,11 @@
 //
 // Planes [F][P] (FP32 unless noted): X, flags (u8), T1, T2 (row sums), C, n, S.
 // Window sums are direct weighted FP32 sums over the clipped window, rows then
-// columns.
+// columns, tiled in shared memory (k_clip_hsum, k_clip_vsum).
 #pragma once
 #include "lpf_filter_stream.cuh"
+
+#include <type_traits>
 
 namespace lpf {
 
@@ -43,66 +45,33 @@ __global__ void k_clip_init(ClipArgs c, const TS* __restrict__ slot) {
     }
 }
 
-// pass 0: T1 = weighted row sums of X m, T2 = of m (m = unflagged);
-// pass 1: T1 = weighted row sums of (X - C)^2 m
-template <int PASS>
-__global__ void k_clip_rows(ClipArgs c, int it) {
-    if (!clip_active(c, it)) return;
-    const int64_t n = (int64_t)c.F * c.H * c.W;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % c.W);
-        const int64_t fy = i / c.W;
-        const int f = (int)(fy / c.H), y = (int)(fy - (int64_t)f * c.H);
-        const int64_t row = (int64_t)f * c.P + (int64_t)y * c.W;
-        float s1 = 0.f, s2 = 0.f;
-        for (int xx = max(x - c.r, 0); xx <= min(x + c.r, c.W - 1); ++xx) {
-            if (c.flags[row + xx]) continue;
-            const float g = __ldg(c.w + abs(xx - x));
-            if (PASS == 0) {
-                s1 = fmaf(g, c.X[row + xx], s1);
-                s2 += g;
-            } else {
-                const float d = c.X[row + xx] - c.C[row + xx];
-                s1 = fmaf(g * d, d, s1);
-            }
-        }
-        c.T1[row + x] = s1;
-        if (PASS == 0) c.T2[row + x] = s2;
-    }
-}
-
-// pass 0: n = weighted column sums of T2, C = weighted column sums of T1 / n
-// (0 where n = 0); pass 1: S = weighted column sums of T1 / n
-template <int PASS>
-__global__ void k_clip_cols(ClipArgs c, int it) {
-    if (!clip_active(c, it)) return;
-    const int64_t n = (int64_t)c.F * c.H * c.W;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % c.W);
-        const int64_t fy = i / c.W;
-        const int f = (int)(fy / c.H), y = (int)(fy - (int64_t)f * c.H);
-        const int64_t base = (int64_t)f * c.P + x;
-        float s1 = 0.f, s2 = 0.f;
-        for (int yy = max(y - c.r, 0); yy <= min(y + c.r, c.H - 1); ++yy) {
-            const float g = __ldg(c.w + abs(yy - y));
-            s1 = fmaf(g, c.T1[base + (int64_t)yy * c.W], s1);
-            if (PASS == 0) s2 = fmaf(g, c.T2[base + (int64_t)yy * c.W], s2);
-        }
-        const int64_t o = base + (int64_t)y * c.W;
-        if (PASS == 0) {
-            c.N[o] = s2;
-            c.C[o] = s2 > 0.f ? s1 / s2 : 0.f;
-        } else {
-            const float cnt = c.N[o];
-            c.S[o] = cnt > 0.f ? s1 / cnt : 0.f;
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------
-// Tiled window sums for R = 7 and 15 (the same sums, in the same ascending tap
-// order, as k_clip_rows / k_clip_cols; those serve the other radii).  R is a
-// compile-time constant, so every tap index and kernel factor is fixed.
+// Tiled window sums, ascending tap order.  R is a compile-time constant
+// (with_radius instantiates 1..16), so every tap index and kernel factor is
+// fixed.
+// f(std::integral_constant<int, r>{}) for a runtime radius r in 1..16
+template <typename Fn>
+void with_radius(int r, Fn&& fn) {
+    switch (r) {
+        case 1: fn(std::integral_constant<int, 1>{}); break;
+        case 2: fn(std::integral_constant<int, 2>{}); break;
+        case 3: fn(std::integral_constant<int, 3>{}); break;
+        case 4: fn(std::integral_constant<int, 4>{}); break;
+        case 5: fn(std::integral_constant<int, 5>{}); break;
+        case 6: fn(std::integral_constant<int, 6>{}); break;
+        case 7: fn(std::integral_constant<int, 7>{}); break;
+        case 8: fn(std::integral_constant<int, 8>{}); break;
+        case 9: fn(std::integral_constant<int, 9>{}); break;
+        case 10: fn(std::integral_constant<int, 10>{}); break;
+        case 11: fn(std::integral_constant<int, 11>{}); break;
+        case 12: fn(std::integral_constant<int, 12>{}); break;
+        case 13: fn(std::integral_constant<int, 13>{}); break;
+        case 14: fn(std::integral_constant<int, 14>{}); break;
+        case 15: fn(std::integral_constant<int, 15>{}); break;
+        default: fn(std::integral_constant<int, 16>{}); break;
+    }
+}
+
 constexpr int kClipHX = 512;            // k_clip_hsum: output columns per CTA (one row)
 constexpr int kClipVX = 64;             // k_clip_vsum: output columns per CTA
 constexpr int kClipVY = 32;             // k_clip_vsum: output rows per CTA

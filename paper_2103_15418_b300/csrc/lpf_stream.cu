@@ -608,29 +608,18 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
                     ca, reinterpret_cast<const __nv_bfloat16*>(s->ring) + ring_slot * n);
                 break;
         }
-        // window sums: shared-memory tiles for radius 7 and 15, direct sums otherwise
+        // window sums: shared-memory tiles, the radius a compile-time constant
         const dim3 gh((unsigned)(((s->W + lpf::kClipHX - 1) / lpf::kClipHX) * s->H), (unsigned)s->F);
         const dim3 gv((unsigned)((s->W + lpf::kClipVX - 1) / lpf::kClipVX),
                       (unsigned)((s->H + lpf::kClipVY - 1) / lpf::kClipVY), (unsigned)s->F);
-        auto tiled = [&](auto h0, auto v0, auto h1, auto v1, int it) {
-            h0<<<gh, 128, 0, s->st>>>(ca, it);
-            v0<<<gv, 128, 0, s->st>>>(ca, it);
-            h1<<<gh, 128, 0, s->st>>>(ca, it);
-            v1<<<gv, 128, 0, s->st>>>(ca, it);
-        };
         for (int it = 0; it < s->prm.clip_iters; ++it) {
-            if (ca.r == 15) {
-                tiled(lpf::k_clip_hsum<15, 0>, lpf::k_clip_vsum<15, 0>, lpf::k_clip_hsum<15, 1>,
-                      lpf::k_clip_vsum<15, 1>, it);
-            } else if (ca.r == 7) {
-                tiled(lpf::k_clip_hsum<7, 0>, lpf::k_clip_vsum<7, 0>, lpf::k_clip_hsum<7, 1>,
-                      lpf::k_clip_vsum<7, 1>, it);
-            } else {
-                lpf::k_clip_rows<0><<<g, 256, 0, s->st>>>(ca, it);
-                lpf::k_clip_cols<0><<<g, 256, 0, s->st>>>(ca, it);
-                lpf::k_clip_rows<1><<<g, 256, 0, s->st>>>(ca, it);
-                lpf::k_clip_cols<1><<<g, 256, 0, s->st>>>(ca, it);
-            }
+            lpf::with_radius(ca.r, [&](auto rc) {
+                constexpr int R = decltype(rc)::value;
+                lpf::k_clip_hsum<R, 0><<<gh, 128, 0, s->st>>>(ca, it);
+                lpf::k_clip_vsum<R, 0><<<gv, 128, 0, s->st>>>(ca, it);
+                lpf::k_clip_hsum<R, 1><<<gh, 128, 0, s->st>>>(ca, it);
+                lpf::k_clip_vsum<R, 1><<<gv, 128, 0, s->st>>>(ca, it);
+            });
             lpf::k_clip_flag<<<dim3((unsigned)std::min<int64_t>((s->HW + 1023) / 1024, 65535), (unsigned)s->F), 256,
                                 0, s->st>>>(ca, it);
         }

@@ -127,15 +127,18 @@ def test_subband_clipping_matches_oracle(lib, dtype):
 
 @pytest.mark.parametrize("dtype,iters,r,H,W", [("fp32", 1, 9, 96, 128), ("fp32", 3, 15, 96, 128),
                                                ("fp16", 1, 15, 96, 128), ("bf16", 3, 7, 96, 128),
-                                               ("fp32", 2, 7, 97, 531), ("fp32", 2, 15, 45, 70)])
+                                               ("fp32", 2, 7, 97, 531), ("fp32", 2, 15, 45, 70),
+                                               ("fp32", 2, 1, 64, 77), ("fp16", 1, 16, 96, 128)])
 def test_subband_gaussian_kernel_matches_oracle(lib, dtype, iters, r, H, W):
     """The per-subband detector with the Gaussian background kernel of Sec. 2.1.1
-    (s = 3 px on the (2r+1)^2 window: r = 7 and 15 take the tiled window sums, 9
-    the direct ones), one pass and clipping iterations, against
+    (s = 3 px on the (2r+1)^2 window, r from 1 to 16), one pass and clipping
+    iterations, against
     clip_detect(..., s): candidates, S/N and per-band statistics; ragged sizes
     (a second 512-column segment, partial 32 x 64 tiles, windows wider than the
     image) included."""
-    spec = synth.spec_aartfaac(H=H, W=W, n_sources=0, n_pulses=0, box_r=r, n_frames=6)
+    # a 3 x 3 Gaussian window caps a lone source's S/N near sqrt(Z) = 2.9: a lower threshold there
+    spec = synth.spec_aartfaac(H=H, W=W, n_sources=0, n_pulses=0, box_r=r, n_frames=6,
+                               kappa=6.0 if r > 2 else 2.5)
     st = synth.SyntheticStream(spec, seed=37)
     s_px, k, matched = 3.0, 3, 0
     with lib.Stream(spec.H, spec.W, spec.freqs_mhz, None, 1, kappa=spec.kappa, box_r=spec.box_r, dtype=dtype,
