@@ -688,3 +688,68 @@ def test_gauss_kernel_wide_limit_is_the_box():
     b = O.clip_detect(D, 4, 4.0, k=2, iters=3)
     assert np.array_equal(a["mask"], b["mask"]) and a["mask"].any()
     assert np.allclose(a["snr"], b["snr"], rtol=0, atol=1e-9)
+
+
+def _factor_sum(img, g, rx, ry):
+    """sum of img over the window clipped to the image, weights g[|dx|] g[|dy|] (a test copy)."""
+    out = np.asarray(img, np.float64)
+    for axis, r in ((1, rx), (0, ry)):
+        a, n = out, out.shape[axis]
+        out = np.zeros_like(a)
+        for k in range(-r, r + 1):
+            dst, src = [slice(None)] * 2, [slice(None)] * 2
+            dst[axis] = slice(max(-k, 0), n - max(k, 0))
+            src[axis] = slice(max(k, 0), n - max(-k, 0))
+            out[tuple(dst)] += g[abs(k)] * a[tuple(src)]
+    return out
+
+
+def _gauss_pins_hold(centre):
+    """The Gaussian kernel's pins for a centre estimate centre(D, m, r, s): the
+    delta response (2-D normalised kernel inside the image) and the masked means
+    with whole 2-D weights at the image edges."""
+    r, s = 4, 1.7
+    D = np.zeros((21, 19))
+    D[10, 9] = 1.0
+    Z = sum(math.exp(-(i * i + j * j) / (2 * s * s)) for i in range(-r, r + 1) for j in range(-r, r + 1))
+    C = centre(D, np.ones_like(D), r, s)
+    ok = all(abs(C[10 + dy, 9 + dx] - math.exp(-(dy * dy + dx * dx) / (2 * s * s)) / Z) < 1e-12
+             for dy in range(-r, r + 1) for dx in range(-r, r + 1))
+    rng = np.random.default_rng(25)
+    X = rng.standard_normal((9, 11))
+    m = np.ones_like(X)
+    m[0, 0] = m[4, 5] = m[8, 3] = 0.0
+    r2, s2 = 3, 1.4
+    C2 = centre(X, m, r2, s2)
+    for y in range(9):
+        for x in range(11):
+            num = den = 0.0
+            for yy in range(max(0, y - r2), min(9, y + r2 + 1)):
+                for xx in range(max(0, x - r2), min(11, x + r2 + 1)):
+                    w = m[yy, xx] * math.exp(-((yy - y) ** 2 + (xx - x) ** 2) / (2 * s2 * s2))
+                    num += w * X[yy, xx]
+                    den += w
+            ok &= abs(C2[y, x] - num / den) < 1e-12
+    return bool(ok)
+
+
+def test_pins_catch_planted_gauss_mistakes():
+    oracle = lambda D, m, r, s: O.kernel_sum(D * m, r, s) / O.kernel_sum(m, r, s)
+    assert _gauss_pins_hold(oracle)
+    fac = lambda r, s, den: np.exp(-np.arange(r + 1) ** 2 / den(s))
+    # s in place of s^2 in the exponent
+    bad_width = lambda D, m, r, s: (_factor_sum(D * m, fac(r, s, lambda s: 2 * s), r, r)
+                                    / _factor_sum(m, fac(r, s, lambda s: 2 * s), r, r))
+    assert not _gauss_pins_hold(bad_width)
+    # normalised by the whole window's weight (no truncation at the edges, no mask)
+    full_z = lambda D, m, r, s: O.kernel_sum(D * m, r, s) / (O.kernel_factors(r, s).sum() ** 2)
+    assert not _gauss_pins_hold(full_z)
+    # flagged pixels left in the normaliser
+    unmasked = lambda D, m, r, s: O.kernel_sum(D * m, r, s) / O.kernel_sum(np.ones_like(m), r, s)
+    assert not _gauss_pins_hold(unmasked)
+    # control: the test's own weighted sums with the right factors pass
+    g = lambda r, s: fac(r, s, lambda s: 2 * s * s)
+    assert _gauss_pins_hold(lambda D, m, r, s: _factor_sum(D * m, g(r, s), r, r) / _factor_sum(m, g(r, s), r, r))
+    # one axis a pixel short
+    short = lambda D, m, r, s: _factor_sum(D * m, g(r, s), r, r - 1) / _factor_sum(m, g(r, s), r, r - 1)
+    assert not _gauss_pins_hold(short)
