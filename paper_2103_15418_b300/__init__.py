@@ -136,6 +136,32 @@ def load(path: Optional[str] = None):
     return lib
 
 
+def _host_frame_ptr(frame, n: int) -> int:
+    """Address of a host frame of n FP32 values in C order (numpy array or CPU
+    tensor).  The library reads exactly 4 n bytes from it, so anything else (a
+    CUDA tensor, another dtype, a strided view, another size) is refused here."""
+    if hasattr(frame, "data_ptr"):
+        if frame.is_cuda:
+            raise ValueError("push_host takes a host frame; use push for a CUDA tensor")
+        if str(frame.dtype) != "torch.float32" or not frame.is_contiguous() or frame.numel() != n:
+            raise ValueError(f"frame must be a contiguous float32 tensor of {n} values")
+        return frame.data_ptr()
+    a = frame
+    if not isinstance(a, np.ndarray) or a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"] or a.size != n:
+        raise ValueError(f"frame must be a C-contiguous float32 array of {n} values")
+    return a.ctypes.data
+
+
+def _out_ptr(out, shape) -> int:
+    """Address of a caller-supplied output: a contiguous FP32 CUDA tensor of
+    exactly this shape (the gather writes prod(shape) values through it)."""
+    if not getattr(out, "is_cuda", False) or str(out.dtype) != "torch.float32" or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float32 CUDA tensor")
+    if tuple(out.shape) != tuple(shape):
+        raise ValueError(f"out has shape {tuple(out.shape)}, expected {tuple(shape)}")
+    return out.data_ptr()
+
+
 def _check(rc: int, what: str):
     if rc != LPF_OK:
         raise LpfError(rc, what)
@@ -221,11 +247,8 @@ class Stream:
         _check(load().lpf_push_frame(self._h, c_void_p(frame.data_ptr()), int(T)), "lpf_push_frame")
 
     def push_host(self, frame, T: int) -> None:
-        """frame: host float32 array/tensor [F, H, W] (pinned for asynchronous copies)."""
-        ptr = frame.data_ptr() if hasattr(frame, "data_ptr") else frame.ctypes.data
-        n = frame.numel() if hasattr(frame, "numel") else frame.size
-        if n != self.F * self.H * self.W:
-            raise ValueError("frame size mismatch")
+        """frame: host float32 array/tensor [F, H, W], C order (pinned for asynchronous copies)."""
+        ptr = _host_frame_ptr(frame, self.F * self.H * self.W)
         _check(load().lpf_push_frame_host(self._h, c_void_p(ptr), int(T)), "lpf_push_frame_host")
 
     def poll(self, cap: Optional[int] = None, timeout_ms: int = -1):
@@ -252,8 +275,9 @@ class Stream:
         n = len(c)
         if out is None:
             out = torch.empty((n, self.F, Tw), dtype=torch.float32, device="cuda")
+        optr = _out_ptr(out, (n, self.F, int(Tw))) if n else 0
         _check(load().lpf_extract_dynspec(self._h, c_void_p(c.ctypes.data) if n else None, n, int(Tw),
-                                          c_void_p(out.data_ptr()) if n else None),
+                                          c_void_p(optr) if n else None),
                "lpf_extract_dynspec")
         if sync:
             self.sync()
@@ -344,6 +368,10 @@ class Server:
     def submit(self, sid: int, frame: np.ndarray, T: int) -> int:
         """Returns LPF_OK or LPF_E_BUSY (retry after a fetch); raises on other errors."""
         fr = np.ascontiguousarray(frame, dtype=np.float32)
+        meta = self._meta.get(int(sid))
+        if meta is not None and fr.size != meta[0] * meta[1] * meta[2]:
+            # the library copies F H W values from the frame
+            raise ValueError(f"frame has {fr.size} values, the stream takes {meta[0] * meta[1] * meta[2]}")
         rc = load().lpf_server_submit(self._h, int(sid), c_void_p(fr.ctypes.data), int(T))
         if rc not in (LPF_OK, LPF_E_BUSY):
             raise LpfError(rc, "lpf_server_submit")

@@ -167,3 +167,39 @@ def test_clipping_footprint():
     # (+ the kernel factors and the statistics partials of the other block layout)
     assert delta <= many - one < delta + 65536
     assert delta <= gauss - one < delta + 65536
+
+
+def test_binding_refuses_buffers_the_library_would_overrun():
+    """push_host reads exactly F H W FP32 values and dynspec writes exactly n F Tw:
+    buffers of another dtype, layout or size are refused before any library call."""
+    n = 2 * 3 * 4
+    ok = np.zeros((2, 3, 4), np.float32)
+    assert lpf._host_frame_ptr(ok, n) == ok.ctypes.data
+    for bad in (np.zeros((2, 3, 4), np.float64), np.zeros((2, 3, 4), np.float16),
+                np.zeros((2, 3, 8), np.float32)[:, :, ::2], np.zeros((2, 3, 5), np.float32), [0.0] * n):
+        with pytest.raises(ValueError):
+            lpf._host_frame_ptr(bad, n)
+    import torch
+    t = torch.zeros((2, 3, 4))
+    assert lpf._host_frame_ptr(t, n) == t.data_ptr()
+    for bad in (t.half(), t.double(), t.transpose(0, 2), torch.zeros(n + 1)):
+        with pytest.raises(ValueError):
+            lpf._host_frame_ptr(bad, n)
+
+    class FakeCuda:                          # shape / dtype / layout of a CUDA tensor, no device
+        is_cuda = True
+
+        def __init__(self, shape, dtype="torch.float32", contiguous=True):
+            self.shape, self.dtype, self._c = shape, dtype, contiguous
+
+        def is_contiguous(self):
+            return self._c
+
+        def data_ptr(self):
+            return 4096
+
+    assert lpf._out_ptr(FakeCuda((5, 16, 12)), (5, 16, 12)) == 4096
+    for bad in (FakeCuda((4, 16, 12)), FakeCuda((5, 16, 12), "torch.float16"),
+                FakeCuda((5, 16, 12), contiguous=False), torch.zeros((5, 16, 12))):
+        with pytest.raises(ValueError):
+            lpf._out_ptr(bad, (5, 16, 12))
