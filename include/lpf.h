@@ -148,9 +148,13 @@ void lpf_default_params(lpf_params* p);
  * on the host (Sec. 3.2) and allocates the ring buffer and scratch on the
  * current CUDA device.
  * F is at most 32, H and W at most 65536, buffer_depth at most 32767.
- * Errors: LPF_E_ARG (sizes <= 0 or above those limits, box_r outside 1..16, lmax_r != 1, bad dtype,
- * non-positive frequency or cadence, negative DM, filter_impl 2 with another box_r), LPF_E_DEPTH (buffer_depth <
- * max delay + 1), LPF_E_OOM, LPF_E_CUDA (no device).
+ * Errors: LPF_E_ARG (sizes <= 0 or above those limits, box_r outside 1..16, lmax_r outside its range
+ * for the mode, bad dtype, non-positive frequency or cadence, negative DM, filter_impl 2 with another
+ * box_r; an unknown mode or kernel; the Gaussian kernel outside the per-subband detector or with
+ * gauss_sigma not positive and finite; the per-subband detector with the box and box_r other than 7 or
+ * 15, or with filter_impl 1; clip_iters outside 1..16, or above 1 outside the per-subband detector;
+ * quality-control thresholds not positive or qc_min_frames < 2), LPF_E_DEPTH (buffer_depth < max delay
+ * + 1), LPF_E_OOM, LPF_E_CUDA (no device).
  */
 int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_mhz,
                     int n_dm, const double* dm_grid, int buffer_depth, const lpf_params* params);
