@@ -753,3 +753,44 @@ def test_pins_catch_planted_gauss_mistakes():
     # one axis a pixel short
     short = lambda D, m, r, s: _factor_sum(D * m, g(r, s), r, r - 1) / _factor_sum(m, g(r, s), r, r - 1)
     assert not _gauss_pins_hold(short)
+
+
+def _clip_pin_holds(clip):
+    """The masked-means pin of iterated clipping for an implementation
+    clip(D, r, kappa, iters) -> (C, S): the second iteration's C and S are the
+    means over the window pixels the first iteration left unflagged."""
+    rng = np.random.default_rng(20)
+    D = rng.standard_normal((14, 15))
+    D[6, 7] += 40.0
+    r, kappa = 2, 4.0
+    flags = O.clip_detect(D, r, kappa, iters=1)["snr"] > kappa
+    C, S = clip(D, r, kappa, 2)
+    H, W = D.shape
+    ok = True
+    for y in range(H):
+        for x in range(W):
+            win = [(yy, xx) for yy in range(max(0, y - r), min(H, y + r + 1))
+                   for xx in range(max(0, x - r), min(W, x + r + 1)) if not flags[yy, xx]]
+            c = sum(D[q] for q in win) / len(win)
+            sq = sum((D[q] - C[q]) ** 2 for q in win) / len(win)
+            ok &= abs(C[y, x] - c) < 1e-12 and abs(S[y, x] - sq) < 1e-12
+    return bool(ok)
+
+
+def test_pins_catch_planted_clip_mistakes():
+    def oracle(D, r, kappa, iters):
+        m = O.clip_detect(D, r, kappa, iters=iters)
+        return m["C"], m["S"]
+    assert _clip_pin_holds(oracle)
+
+    def first_pass_only(D, r, kappa, iters):              # never re-estimates
+        return oracle(D, r, kappa, 1)
+    assert not _clip_pin_holds(first_pass_only)
+
+    def full_count(D, r, kappa, iters):                   # masked sums over the whole window's count
+        flags = O.clip_detect(D, r, kappa, iters=1)["snr"] > kappa
+        m = (~flags).astype(float)
+        n = O.window_count(*D.shape, r)
+        C = O.box_sum(D * m, r) / n
+        return C, O.box_sum((D - C) ** 2 * m, r) / n
+    assert not _clip_pin_holds(full_count)
