@@ -9,6 +9,10 @@ per-trial stats).  Metric: pixel * DM-trials per second (H*W*N_DM per frame).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype fp32|fp16|bf16]
   python bench.py --impl reference ...     # the FP64 CPU oracle on the same metric
+  python bench.py --workload serving|subband|stress
+
+The default line also carries an FP16-storage measurement of the same workload
+("fp16") and a short replay of the four-stream serving mix ("serving").
 
 Under torchrun (N > 1) every rank runs an independent stream on its own GPU
 (weak scaling, no collective on the data path); rank 0 prints the JSON line.
@@ -16,11 +20,14 @@ Under torchrun (N > 1) every rank runs an independent stream on its own GPU
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
+import multiprocessing as mp
 import os
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 import numpy as np
@@ -33,6 +40,7 @@ import synth  # noqa: E402
 RESULT_SLOTS = 4                # result slots: up to 3 frames ahead of the oldest unpolled one
 METRIC = "pixel*DM-trials/s"
 WORKLOAD = "aartfaac-1024x1024-16sb-251dm-depth48-box31"
+DTYPE_NAME = {"fp32": "f32", "fp16": "f16", "bf16": "bf16"}
 
 
 def parse():
@@ -44,6 +52,9 @@ def parse():
     ap.add_argument("--dtype", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp16", action="store_true", help="skip the FP16-storage sub-measurement")
+    ap.add_argument("--serve-seconds", type=float, default=12.0,
+                    help="length of the serving-mix replay in the default line (0: skip)")
     ap.add_argument("--pool", type=int, default=12, help="distinct synthetic frames cycled")
     ap.add_argument("--clip-iters", type=int, default=1,
                     help="subband workload: sigma-clip iterations (1 = one pass)")
@@ -53,9 +64,10 @@ def parse():
     ap.add_argument("--qc", action="store_true",
                     help="quality control of every frame before the search (band and pixel scores)")
     ap.add_argument("--workload", default="aartfaac", choices=["aartfaac", "serving", "subband", "stress"],
-                    help="serving: four concurrent FP16 streams through the C++ serving loop")
+                    help="serving: the four-stream FP16 mix through the C++ serving loop")
     ap.add_argument("--cadence", type=float, default=1.0, help="serving: frame cadence in seconds")
-    ap.add_argument("--frames", type=int, default=60, help="serving: frames per stream")
+    ap.add_argument("--seconds", type=float, default=600.0, help="serving: length of the replay")
+    ap.add_argument("--jitter", type=float, default=0.05, help="serving: arrival jitter, +- seconds")
     return ap.parse_args()
 
 
@@ -107,25 +119,23 @@ def kernel_traffic(field="dram_bytes_per_launch"):
     return out
 
 
-def algorithmic_bytes(spec, delays, n_distinct):
-    """Bytes a push must move at minimum, per stage, with storage type of b bytes."""
-    b = 4 if spec.dtype == "fp32" else 2
+def algorithmic_bytes(spec, delays, dtype):
+    """Bytes a push must move at minimum (algorithmic count): the ring
+    reads sum_f U_f H W b (every distinct delay plane read once) plus the ingest of
+    the frame (F H W FP32 read, F H W b written); b = storage bytes."""
+    b = 4 if dtype == "fp32" else 2
     HW = spec.H * spec.W
     lags = delays.max(axis=1)[:, None] - delays
     U = sum(len(np.unique(lags[:, f])) for f in range(spec.F))
     ring_reads = U * HW * b
-    return dict(
-        path=ring_reads + spec.F * HW * (4 + b),
-        ingest=spec.F * HW * (4 + b),
-        dedisperse=ring_reads + n_distinct * HW * 4,
-        filter_detect=n_distinct * HW * 4,
-        U=U,
-    )
+    ingest = spec.F * HW * (4 + b)
+    return dict(path=ring_reads + ingest, ring_reads=ring_reads, ingest=ingest, U=U)
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling (10 ms) of SM clocks and throttle reasons, started before
+    the ring fill; summary() keeps the samples taken inside a wall-clock window."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -133,18 +143,19 @@ class Clocks:
         self.index = index
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.p = None
+        self.rows = None
 
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "50"],
+                                       "--format=csv,noheader,nounits", "-lms", "10"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
 
     def stop(self):
         if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
@@ -155,39 +166,134 @@ class Clocks:
         with open(self.f.name) as fh:
             for line in fh:
                 parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    continue
+                rows.append([ts] + parts[1:])
         os.unlink(self.f.name)
+        self.rows = rows
+
+    def summary(self, t0, t1):
+        """Samples inside [t0, t1]; if that window is shorter than the sampling period,
+        the samples within 0.5 s of it (the same pushes, warm-up and e2e loop)."""
+        if self.p is None or self.rows is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        win = "timed region"
+        rows = [r for r in self.rows if t0 <= r[0] <= t1]
+        if len(rows) < 3:
+            rows = [r for r in self.rows if t0 - 0.5 <= r[0] <= t1 + 0.5]
+            win = "timed region +- 0.5 s (warm-up and end-to-end pushes of the same stream)"
         if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        num = lambda v: v.replace(".", "", 1).isdigit()
+        sm = [float(r[2]) for r in rows if num(r[2])]
+        mx = [float(r[3]) for r in rows if num(r[3])]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "window": win, "period_ms": 10}
 
 
-def oracle_sample(spec, frame_at, T, delays, dms):
+# ---------------------------------------------------------------------------
+# The FP64 oracle on the host cores (cpu_baseline and the reference arm): one
+# spawned worker process per core; each step hands every worker DM trials of one
+# push, the workers build the frames they read (untimed), meet at a barrier and
+# run the oracle's search_push on their trials (timed).  The step's time is the
+# first start to the last finish.
+class _PlaneFrame:
+    def __init__(self, planes, t):
+        self.planes, self.t = planes, t
+
+    def __getitem__(self, f):
+        return self.planes[(self.t, f)]
+
+
+def _oracle_worker(wid, dtype, seed, barrier, tasks, results):
+    import synth as S
     from oracle import lpf_oracle as O
-    t = time.perf_counter()
-    O.search_push(frame_at, T, delays, spec.box_r, spec.kappa, dms=dms)
-    return time.perf_counter() - t
+    spec = S.spec_aartfaac(dtype=dtype)
+    st = S.SyntheticStream(spec, seed=seed)
+    delays = O.delay_table(spec.freqs_mhz, spec.dm_grid, spec.cadence_s)
+    dmax = delays.max(axis=1)
+    while True:
+        task = tasks.get()
+        if task is None:
+            return
+        T, dms = task
+        need = {}
+        for d in dms:
+            for f in range(spec.F):
+                need.setdefault(int(T - dmax[d] + delays[d, f]), set()).add(f)
+        planes = {}
+        for t, fs in need.items():
+            x = st.frame(t)
+            for f in fs:
+                planes[(t, f)] = O.storage_round(x[f], dtype) if dtype != "fp32" else x[f].astype(np.float64)
+        barrier.wait()
+        t_a = time.time()
+        if dms:
+            O.search_push(lambda t: _PlaneFrame(planes, t), T, delays, spec.box_r, spec.kappa, dms=dms)
+        t_b = time.time()
+        results.put((wid, t_a, t_b, len(dms)))
 
 
-def cpu_baseline(spec, st, delays, n_dm=36):
-    """The FP64 oracle (as it stands, one process) on a bounded sample of one push."""
-    import functools
-    fa = functools.lru_cache(maxsize=64)(lambda t: st.frame(t).astype(np.float64))
-    T = int(delays.max())
-    dms = [int(d) for d in np.linspace(0, spec.n_dm - 1, n_dm).round()]
-    fa_warm = [fa(T - k) for k in range(int(delays.max()) + 1)]  # generation outside the timing
-    del fa_warm
-    secs = oracle_sample(spec, fa, T, delays, dms)
-    val = spec.H * spec.W * len(dms) / secs
-    return {"value": val, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"one push (T={T}) of the {spec.H}x{spec.W} stream, {len(dms)} of "
-                      f"{spec.n_dm} DM trials, FP64 NumPy single process, {secs:.1f} s"}
+class OraclePool:
+    def __init__(self, dtype, seed=1, max_workers=48):
+        avail = len(os.sched_getaffinity(0))
+        try:
+            mem_gb = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_AVPHYS_PAGES") / 2 ** 30
+        except (ValueError, OSError):
+            mem_gb = 16.0
+        # about 0.5 GB per worker at 1024^2 (its planes and the oracle's temporaries)
+        self.n = max(1, min(avail, max_workers, int(mem_gb / 0.5)))
+        ctx = mp.get_context("spawn")
+        self.barrier = ctx.Barrier(self.n)
+        self.tasks = [ctx.Queue() for _ in range(self.n)]
+        self.results = ctx.Queue()
+        self.procs = [ctx.Process(target=_oracle_worker, args=(i, dtype, seed, self.barrier, self.tasks[i],
+                                                               self.results), daemon=True)
+                      for i in range(self.n)]
+        for p in self.procs:
+            p.start()
+
+    def step(self, T, trials):
+        """trials: one list of DM trials per worker.  Returns (seconds, trials run)."""
+        for q, tr in zip(self.tasks, trials):
+            q.put((int(T), [int(d) for d in tr]))
+        res = [self.results.get(timeout=1800) for _ in range(self.n)]
+        return max(r[2] for r in res) - min(r[1] for r in res), sum(r[3] for r in res)
+
+    def close(self):
+        for q in self.tasks:
+            q.put(None)
+        for p in self.procs:
+            p.join(timeout=30)
+
+
+def spread_trials(n_dm, n_workers, per_worker, offset=0):
+    """per_worker DM trials for each worker, spread over the grid."""
+    k = n_workers * per_worker
+    picks = [int(v) % n_dm for v in np.linspace(0, n_dm - 1, k).round() + offset]
+    return [picks[i::n_workers] for i in range(n_workers)]
+
+
+def cpu_baseline(spec, delays, per_worker=2):
+    """The FP64 oracle (as it stands) on the host cores: one push, per_worker DM trials
+    per worker process."""
+    pool = OraclePool(spec.dtype)
+    try:
+        T = int(delays.max())
+        secs, n = pool.step(T, spread_trials(spec.n_dm, pool.n, per_worker))
+    finally:
+        pool.close()
+    return {"value": spec.H * spec.W * n / secs, "unit": METRIC, "cores": pool.n, "kind": "oracle",
+            "sample": f"one push (T={T}) of the {spec.H}x{spec.W} stream: {n} of {spec.n_dm} DM trials, "
+                      f"{per_worker} per process, FP64 NumPy in {pool.n} spawned processes on "
+                      f"{pool.n} host cores, {secs:.1f} s wall"}
 
 
 def run_reference(args):
@@ -196,33 +302,131 @@ def run_reference(args):
         return
     spec = workload_spec(args.dtype)
     from oracle import lpf_oracle as O
-    import functools
-    st = synth.SyntheticStream(spec, seed=1)
     delays = O.delay_table(spec.freqs_mhz, spec.dm_grid, spec.cadence_s)
-    fa = functools.lru_cache(maxsize=128)(lambda t: O.storage_round(st.frame(t), spec.dtype))
     T0 = int(delays.max())
-    per_step = 2    # DM trials per step: the oracle's bounded sample of one push
-    for w in range(args.warmup):
-        for k in range(int(delays.max()) + 1):
-            fa(T0 + w - k)
-    tot = 0.0
-    for k in range(args.steps):
-        T = T0 + (k % 4)
-        for j in range(int(delays.max()) + 1):
-            fa(T - j)
-        dms = [(k * per_step + j) % spec.n_dm for j in range(per_step)]
-        tot += oracle_sample(spec, fa, T, delays, dms)
-    val = spec.H * spec.W * per_step * args.steps / tot
-    sample = (f"each step: {per_step} of {spec.n_dm} DM trials of one push of the "
-              f"{spec.H}x{spec.W} stream, FP64 NumPy single process")
+    pool = OraclePool(spec.dtype)
+    # one DM trial per worker per step; fewer workers per step for long runs, so that
+    # the whole run stays within a few minutes
+    per_step = pool.n if args.steps <= 40 else max(1, pool.n * 40 // args.steps)
+    try:
+        def trials(k):
+            sel = spread_trials(spec.n_dm, per_step, 1, offset=k)
+            return sel + [[] for _ in range(pool.n - per_step)]
+        for w in range(args.warmup):
+            pool.step(T0, trials(w))
+        tot, n_tot = 0.0, 0
+        for k in range(args.steps):
+            secs, n = pool.step(T0 + (k % 4), trials(k))
+            tot += secs
+            n_tot += n
+    finally:
+        pool.close()
+    val = spec.H * spec.W * n_tot / tot
+    sample = (f"each step: {per_step} of {spec.n_dm} DM trials of one push of the {spec.H}x{spec.W} stream, "
+              f"one per process, FP64 NumPy in {pool.n} spawned processes on {pool.n} host cores")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "storage": args.dtype,
                                             "sample_dm_per_step": per_step},
-            "cpu_baseline": {"value": val, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": val, "unit": METRIC, "cores": pool.n, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def measure(lpf, torch, dev, spec, dtype, steps, warmup, pool_n, seed, qc=False, e2e_steps=0, dist=None):
+    """Device-timed steps of one stream (and, with e2e_steps, the end-to-end loop with
+    host buffers).  The ring is filled first, so every trial is active."""
+    st = synth.SyntheticStream(spec, seed=seed)
+    pool = [torch.from_numpy(st.frame(t)) for t in range(pool_n)]
+    pool_dev = [p.to(dev) for p in pool]
+    pool_pin = [p.pin_memory() for p in pool] if e2e_steps else []
+    cur = torch.cuda.Stream(dev)            # the search stream (the timing events are recorded on it)
+    s = lpf.Stream(spec.H, spec.W, spec.freqs_mhz, spec.dm_grid, spec.depth, kappa=spec.kappa,
+                   box_r=spec.box_r, dtype=dtype, result_slots=RESULT_SLOTS, cuda_stream=cur,
+                   qc=qc, qc_min_frames=16)
+    out = {"info": s.info(), "delays": s.delay_table()}
+    T = 0
+    polled = []
+
+    def push(T):
+        s.push(pool_dev[T % pool_n], T)
+
+    def poll():
+        _, c, n, _ = s.poll(timeout_ms=600000)
+        polled.append(n)
+
+    for _ in range(spec.depth + warmup):
+        push(T)
+        T += 1
+        poll()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    s.kernel_times(reset=True)
+    s.set_profiling(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    # result_slots - 1 pushes ahead of the oldest unpolled frame, as in the
+    # end-to-end loop below
+    ahead = max(1, RESULT_SLOTS - 1)
+    out["t_wall0"] = time.time()
+    ev0.record(cur)
+    for k in range(steps):
+        push(T)
+        T += 1
+        if k >= ahead:
+            poll()
+    for _ in range(ahead):
+        poll()
+    ev1.record(cur)
+    torch.cuda.synchronize()
+    out["t_wall1"] = time.time()
+    s.set_profiling(False)
+    out["elapsed"] = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dist, dev)
+    kt = s.kernel_times(reset=True)
+    out["per_push"] = {n: kt[n][0] / max(kt[n][1], 1) for n in kt}
+    out["ncand"] = float(np.mean(polled[-steps:]))
+    if e2e_steps:
+        # end to end through the C ABI with host buffers: H2D of the frame, D2H of the
+        # candidates, as a user streams frames: push frame T, then poll the oldest
+        # frame once result_slots - 1 frames are in flight (the upload of T overlaps
+        # the search of T - 1); latency is push call -> poll return of the same frame
+        lat, e2e_cands, t_push = [], [], {}
+        inflight = max(1, RESULT_SLOTS - 1)
+
+        def poll_host():
+            Tp, c, n, _ = s.poll(timeout_ms=600000)
+            e2e_cands.append(n)
+            lat.append(time.perf_counter() - t_push.pop(Tp))
+
+        torch.cuda.synchronize()
+        t_e0 = time.perf_counter()
+        for k in range(e2e_steps):
+            t_push[T] = time.perf_counter()
+            s.push_host(pool_pin[T % pool_n], T)
+            T += 1
+            if len(t_push) >= inflight + 1:
+                poll_host()
+        while t_push:
+            poll_host()
+        out["e2e_s"] = max_over_ranks(time.perf_counter() - t_e0, dist, dev)
+        out["lat"], out["e2e_cands"] = lat, e2e_cands
+        out["t_wall1e"] = time.time()
+    s.close()
+    return out
+
+
+def path_roofline(spec, dtype, delays, ms_per_step, hbm_peak, peak_src, traffic=None):
+    nb = algorithmic_bytes(spec, delays, dtype)
+    ach = nb["path"] / (ms_per_step / 1e3) / 1e9
+    return {"kernel": "whole push (ingest, shift-sum, filter, detect; the step)", "bound": "hbm",
+            "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "peak_source": peak_src,
+            "traffic": traffic, "algorithmic_bytes_per_step": nb["path"],
+            "note": "algorithmic bytes: sum over subbands of the distinct delay planes read once "
+                    f"({nb['U']} planes) + ingest of the frame; CUDA-event time of the whole step"}
 
 
 def run_ours(args):
@@ -236,100 +440,27 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    spec = workload_spec(args.dtype)
-    st = synth.SyntheticStream(spec, seed=1 + rank)
-    pool = [torch.from_numpy(st.frame(t)) for t in range(args.pool)]
-    pool_dev = [p.to(dev) for p in pool]
-    pool_pin = [p.pin_memory() for p in pool]
-    cur = torch.cuda.Stream(dev)            # the search stream (the timing events are recorded on it)
-    s = lpf.Stream(spec.H, spec.W, spec.freqs_mhz, spec.dm_grid, spec.depth, kappa=spec.kappa,
-                   box_r=spec.box_r, dtype=args.dtype, result_slots=RESULT_SLOTS, cuda_stream=cur,
-                   qc=args.qc, qc_min_frames=16)
-    info = s.info()
-    delays = s.delay_table()
-    nbytes = algorithmic_bytes(spec, delays, info["n_distinct"])
-    depth = spec.depth
-    T = 0
-    polled = []
-
-    def push(T):
-        s.push(pool_dev[T % args.pool], T)
-
-    def poll():
-        _, c, n, _ = s.poll(timeout_ms=600000)
-        polled.append(n)
-
-    # fill the ring so every trial is active, then warm up
-    for _ in range(depth + args.warmup):
-        push(T)
-        T += 1
-        poll()
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
     clocks = Clocks(local)
-    clocks.start()
-    s.kernel_times(reset=True)
-    s.set_profiling(True)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    # result_slots - 1 pushes ahead of the oldest unpolled frame, as in the
-    # end-to-end loop below
-    ahead = max(1, RESULT_SLOTS - 1)
-    ev0.record(cur)
-    for k in range(args.steps):
-        push(T)
-        T += 1
-        if k >= ahead:
-            poll()
-    for _ in range(ahead):
-        poll()
-    ev1.record(cur)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    s.set_profiling(False)
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    ktimes = s.kernel_times(reset=True)
-    elapsed = max_over_ranks(elapsed, dist, dev)
-    ncand = float(np.mean(polled[-args.steps:]))
-    pix_dm = spec.H * spec.W * spec.n_dm
-    value = pix_dm * args.steps * ws / elapsed
-
-    # end to end through the C ABI with host buffers: H2D of the frame, D2H of the
-    # candidates, as a user streams frames: push frame T, then poll the oldest
-    # frame once result_slots - 1 frames are in flight (the upload of T overlaps
-    # the search of T - 1); latency is push call -> poll return of the same frame
-    lat = []
-    e2e_cands = []
-    t_push = {}
-    inflight = max(1, RESULT_SLOTS - 1)
-
-    def poll_host():
-        Tp, c, n, _ = s.poll(timeout_ms=600000)
-        e2e_cands.append(n)
-        lat.append(time.perf_counter() - t_push.pop(Tp))
-
-    torch.cuda.synchronize()
-    t_e0 = time.perf_counter()
-    for k in range(args.e2e_steps):
-        t_push[T] = time.perf_counter()
-        s.push_host(pool_pin[T % args.pool], T)
-        T += 1
-        if len(t_push) >= inflight + 1:
-            poll_host()
-    while t_push:
-        poll_host()
-    e2e_s = time.perf_counter() - t_e0
-    e2e_s = max_over_ranks(e2e_s, dist, dev)
-    e2e_value = pix_dm * args.e2e_steps * ws / e2e_s
-    s.close()
-
+    clocks.start()                     # before the ring fill, so the short timed region has samples
+    spec = workload_spec(args.dtype)
+    m = measure(lpf, torch, dev, spec, args.dtype, args.steps, args.warmup, args.pool, 1 + rank, qc=args.qc,
+                e2e_steps=args.e2e_steps, dist=dist)
+    f16 = None
+    if not args.no_fp16 and args.dtype == "fp32" and not args.qc:
+        f16 = measure(lpf, torch, dev, workload_spec("fp16"), "fp16", args.steps, args.warmup, args.pool,
+                      1 + rank, dist=dist)
+    clocks.stop()
+    serving = None
+    if rank == 0 and ws == 1 and args.serve_seconds > 0:
+        serving = serve_mix(lpf, seconds=args.serve_seconds, cadence=1.0, jitter=0.05)
     if rank != 0:
         return
-    # per-kernel rooflines from the CUDA-event stage times (on the launching stream)
-    names = list(ktimes)
-    per_push = {n: ktimes[n][0] / max(ktimes[n][1], 1) for n in names}
+    info, delays, per_push = m["info"], m["delays"], m["per_push"]
+    elapsed = m["elapsed"]
+    pix_dm = spec.H * spec.W * spec.n_dm
+    value = pix_dm * args.steps * ws / elapsed
+    ms_step = 1e3 * elapsed / args.steps
+    e2e_value = pix_dm * args.e2e_steps * ws / m["e2e_s"] if args.e2e_steps else None
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -343,17 +474,18 @@ def run_ours(args):
     traffic = kernel_traffic()
     HW = spec.H * spec.W
     nd = info["n_distinct"]
-    n_dd = 1                                              # residual ring -> D - C
-    dd_ms = per_push["dedisperse"] / n_dd
-    dd_bytes = nbytes["dedisperse"]
-    dd_ach = dd_bytes / (dd_ms / 1e3) / 1e9
-    f_ms = per_push["filter_detect"]
-    f_ops = FILTER_OPS_PER_PIXEL_TRIAL * HW * nd
-    f_ach = f_ops / (f_ms / 1e3) / 1e12
+    nb = algorithmic_bytes(spec, delays, args.dtype)
+    # the shift-sum: its algorithmic bytes are the ring reads only (the D - C images it
+    # writes are an intermediate of this design, not work the method requires)
+    dd_ms = per_push["dedisperse"]
+    dd_ach = nb["ring_reads"] / (dd_ms / 1e3) / 1e9
     roof_dd = {"kernel": "k_dedisperse (shift-sum)", "bound": "hbm", "achieved": dd_ach, "peak": hbm_peak,
                "unit": "GB/s", "frac": dd_ach / hbm_peak, "peak_source": peak_src,
                "traffic": traffic.get("k_dedisperse_" + args.dtype),
-               "algorithmic_bytes_per_launch": dd_bytes, "avg_launch_ms": dd_ms, "launches_per_step": n_dd}
+               "algorithmic_bytes_per_launch": nb["ring_reads"], "avg_launch_ms": dd_ms, "launches_per_step": 1}
+    f_ms = per_push["filter_detect"]
+    f_ops = FILTER_OPS_PER_PIXEL_TRIAL * HW * nd
+    f_ach = f_ops / (f_ms / 1e3) / 1e12
     roof_f = {"kernel": "k_filter_res<15> (box spread, S/N, threshold, stats)", "bound": "alu",
               "achieved": f_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": f_ach / alu_peak,
               "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
@@ -369,57 +501,158 @@ def run_ours(args):
                     "frac": f_inst / (f_ms / 1e3) / 1e12 / issue_peak if f_inst else None,
                     "peak_source": f"{sms} SMs x 4 schedulers x {sm_mhz:.0f} MHz",
                     "warp_instructions_per_launch": f_inst, "avg_launch_ms": f_ms}
-    roof = roof_f if f_ms >= dd_ms else roof_dd
-    # quality control + ingest (k_qc_scan, k_qc_decide, k_residual, k_ingest_qc): the
-    # QC passes read the frame and the running mean and m2 twice and write them once
-    b = 4 if args.dtype == "fp32" else 2
-    qc_bytes = spec.F * HW * (12 + 20 + b)
-    qc_ms = per_push["ingest"] + per_push.get("ring_write", 0.0)
-    roof_qc = {"kernel": "quality control + ingest (k_qc_scan, k_qc_decide, k_ingest_qc, k_residual)",
-               "bound": "hbm", "achieved": qc_bytes / (qc_ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
-               "frac": qc_bytes / (qc_ms / 1e3) / 1e9 / hbm_peak, "peak_source": peak_src, "traffic": None,
-               "algorithmic_bytes_per_launch": qc_bytes, "avg_launch_ms": qc_ms, "launches_per_step": 1,
-               "note": "the stage also runs k_residual (per-subband X - C(X)), not counted in the bytes"}
-    path_ach = nbytes["path"] / (elapsed / args.steps) / 1e9
+    step_traffic = None
+    tr_keys = ["k_dedisperse_" + args.dtype, "k_filter_res"]
+    if all(traffic.get(k) for k in tr_keys):
+        # DRAM bytes of the main-stream kernels that move the bulk (ncu, one launch each)
+        step_traffic = sum(traffic[k] for k in tr_keys)
+    roof = path_roofline(spec, args.dtype, delays, ms_step, hbm_peak, peak_src, step_traffic)
+    if step_traffic:
+        roof["traffic_note"] = "ncu DRAM bytes of k_dedisperse + k_filter_res per push"
+    rooflines = [roof, roof_dd, roof_f, roof_f_issue]
+    if args.qc:
+        # quality control + ingest (k_qc_scan, k_qc_decide, k_residual, k_ingest_qc): the
+        # QC passes read the frame and the running mean and m2 twice and write them once
+        b = 4 if args.dtype == "fp32" else 2
+        qc_bytes = spec.F * HW * (12 + 20 + b)
+        qc_ms = per_push["ingest"] + per_push.get("ring_write", 0.0)
+        rooflines.append({"kernel": "quality control + ingest (k_qc_scan, k_qc_decide, k_ingest_qc, k_residual)",
+                          "bound": "hbm", "achieved": qc_bytes / (qc_ms / 1e3) / 1e9, "peak": hbm_peak,
+                          "unit": "GB/s", "frac": qc_bytes / (qc_ms / 1e3) / 1e9 / hbm_peak,
+                          "peak_source": peak_src, "traffic": None, "algorithmic_bytes_per_launch": qc_bytes,
+                          "avg_launch_ms": qc_ms, "launches_per_step": 1})
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[args.dtype],
         "data": "synthetic (seeded AARTFAAC-shaped stream: noise, 3-sigma cosine gradient, "
                 "500 Gaussian-PSF sources, 20 dispersed pulses)",
         "config": {"workload": WORKLOAD, "H": spec.H, "W": spec.W, "subbands": spec.F,
-                   "dm_trials": spec.n_dm, "depth": depth, "box": 2 * spec.box_r + 1,
-                   "storage": args.dtype, "distinct_delay_rows": info["n_distinct"],
-                   "quality_control": bool(args.qc),
+                   "dm_trials": spec.n_dm, "depth": spec.depth, "box": 2 * spec.box_r + 1,
+                   "storage": args.dtype, "arithmetic": "f32 (delay table f64, statistics f64)",
+                   "distinct_delay_rows": nd, "quality_control": bool(args.qc),
                    "l2": "inputs larger than L2 (ring %.2f GB)" % (info["ring_bytes"] / 1e9),
                    "parallelism": f"{ws} independent stream(s), one per GPU"},
-        "e2e": {"value": e2e_value, "unit": METRIC,
-                "h2d_bytes_per_step": spec.F * spec.H * spec.W * 4,
-                "d2h_bytes_per_step": int(np.mean(e2e_cands) * 24 + spec.n_dm * 16)},
-        "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
-                       "p99": 1e3 * float(np.percentile(lat, 99)),
-                       "what": f"push_frame_host -> poll of the same frame, up to {RESULT_SLOTS} frames in flight"},
-        # per push: ingest + residual, counter reset, shift-sum, filter, 3x3 maximum,
-        # 3 per sort pass, format, stats
-        "gpu_launches": int(args.steps * (8 + 3 * _passes(spec) + (2 if args.qc else 0))),
+        "gpu_launches": int(args.steps * launches_per_push(spec, args.qc)),
         "roofline": roof,
-        "rooflines": [roof_f, roof_f_issue, roof_dd] + ([roof_qc] if args.qc else []),
-        "path_roofline": {"bound": "hbm", "achieved": path_ach, "peak": hbm_peak, "unit": "GB/s",
-                          "frac": path_ach / hbm_peak,
-                          "algorithmic_bytes_per_step": nbytes["path"],
-                          "note": "sum over subbands of distinct delay planes read once + ingest"},
+        "rooflines": rooflines,
         "kernel_ms_per_step": per_push,
-        "candidates_per_step": ncand,
-        "clocks": clk,
+        "candidates_per_step": m["ncand"],
+        "clocks": clocks.summary(m["t_wall0"], m["t_wall1"]),
     }
+    if e2e_value is not None:
+        line["e2e"] = {"value": e2e_value, "unit": METRIC,
+                       "h2d_bytes_per_step": spec.F * spec.H * spec.W * 4,
+                       "d2h_bytes_per_step": int(np.mean(m["e2e_cands"]) * 24 + spec.n_dm * 16)}
+        line["latency_ms"] = {"p50": 1e3 * float(np.percentile(m["lat"], 50)),
+                              "p99": 1e3 * float(np.percentile(m["lat"], 99)),
+                              "what": f"push_frame_host -> poll of the same frame, up to {RESULT_SLOTS} "
+                                      "frames in flight"}
+    if f16 is not None:
+        sp16 = workload_spec("fp16")
+        ms16 = 1e3 * f16["elapsed"] / args.steps
+        line["fp16"] = {"storage": "fp16", "ms_per_step": ms16, "value": pix_dm * args.steps * ws / f16["elapsed"],
+                        "speedup_vs_fp32": ms_step / ms16,
+                        "roofline": path_roofline(sp16, "fp16", f16["delays"], ms16, hbm_peak, peak_src),
+                        "kernel_ms_per_step": f16["per_push"], "candidates_per_step": f16["ncand"],
+                        "clocks": clocks.summary(f16["t_wall0"], f16["t_wall1"])}
+    if serving is not None:
+        line["serving"] = serving
     if ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(spec, st, delays)
+        line["cpu_baseline"] = cpu_baseline(spec, delays)
     print(json.dumps(line), flush=True)
 
 
-def _passes(spec):
+def launches_per_push(spec, qc):
+    """Kernels of one push: residuals, counter reset, shift-sum, ring write, filter,
+    3x3 pass, 3 per ordering pass, formatting, statistics (+ 2 with quality control)."""
     bits = lambda v: max(1, int(np.ceil(np.log2(v))))
-    return (bits(spec.W) + bits(spec.H) + bits(spec.n_dm) + 7) // 8
+    passes = (bits(spec.W) + bits(spec.H) + bits(spec.n_dm) + 7) // 8
+    return 8 + 3 * passes + (2 if qc else 0)
+
+
+# ---------------------------------------------------------------------------
+def serve_mix(lpf, seconds, cadence, jitter, seed=7):
+    """The four-stream FP16 serving mix replayed through the C++ serving loop: the
+    2048^2/16/501 and 1024^2/16/251 streams and a 512^2/8/128 stream for the whole
+    replay; a second 512^2 stream for its first half, closed there, and a third
+    opened in its place for the second half (four live streams throughout).  Frame
+    T of a stream is submitted at (T + k/4) * cadence +- jitter (uniform, seeded).
+    Reports submit -> fetch latency (the fetching thread's wall clock) and the
+    aggregate pixel * DM-trials/s served."""
+    specs = synth.spec_serving_mix()
+    late = synth.StreamSpec(**{**specs[3].__dict__, "name": "mix-512c"})
+    n = max(2, int(round(seconds / cadence)))
+    half = n // 2
+    # (spec, first frame slot, frames): the slot is the cadence tick of its frame 0
+    plan = [(specs[0], 0, n), (specs[1], 0, n), (specs[2], 0, n), (specs[3], 0, half), (late, half, n - half)]
+    pools = []
+    for i, (sp, _, _) in enumerate(plan):
+        st = synth.SyntheticStream(sp, seed=60 + i)
+        pools.append([st.frame(t) for t in range(4)])
+    budget = 80 << 30
+    rng = np.random.default_rng(seed)
+    lat = {i: [] for i in range(len(plan))}
+    submit_t = {}
+    lock = threading.Lock()
+    with lpf.Server(budget, max_streams=8) as srv:
+        ids = [None] * len(plan)
+
+        def drain(i, count):
+            while ids[i] is None:
+                time.sleep(0.001)
+            for _ in range(count):
+                T, c, nf, _ = srv.fetch(ids[i], timeout_ms=600000)
+                t = time.perf_counter()
+                with lock:
+                    lat[i].append(1e3 * (t - submit_t.pop((i, T))))
+        events = []
+        for i, (sp, first, cnt) in enumerate(plan):
+            for T in range(cnt):
+                events.append(((first + T + i / 4.0) * cadence + rng.uniform(-jitter, jitter), i, T))
+        events.sort()
+        threads = [threading.Thread(target=drain, args=(i, cnt)) for i, (_, _, cnt) in enumerate(plan)]
+        for th in threads:
+            th.start()
+        t0 = time.perf_counter()
+        for due, i, T in events:
+            sp, first, cnt = plan[i]
+            if ids[i] is None:
+                ids[i] = srv.open_stream(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth, kappa=sp.kappa,
+                                         box_r=sp.box_r, dtype=sp.dtype)
+            wait = t0 + max(due, 0.0) - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            while True:
+                with lock:
+                    submit_t[(i, T)] = time.perf_counter()
+                if srv.submit(ids[i], pools[i][T % 4], T) != lpf.LPF_E_BUSY:
+                    break
+                time.sleep(0.0005)
+            if T == cnt - 1 and cnt < n:
+                srv.close_stream(ids[i])          # stream leaves mid-replay
+        for th in threads:
+            th.join()
+        wall = time.perf_counter() - t0
+        st_all = srv.stats()
+    all_lat = np.concatenate([np.asarray(v) for v in lat.values()])
+    pixdm = sum(sp.H * sp.W * sp.n_dm * cnt for sp, _, cnt in plan)
+    return {"workload": "serving-mix-4-streams-fp16 (2048^2/16/501, 1024^2/16/251, 512^2/8/128, "
+                        "512^2/8/128 closed at half time and replaced by a third)",
+            "seconds": seconds, "cadence_s": cadence, "jitter_s": jitter, "frames": int(len(all_lat)),
+            "p50_ms": float(np.percentile(all_lat, 50)), "p99_ms": float(np.percentile(all_lat, 99)),
+            "max_ms": float(all_lat.max()),
+            "per_stream_p99_ms": {plan[i][0].name: float(np.percentile(v, 99)) for i, v in lat.items() if v},
+            "pixel_dm_per_s": pixdm / wall, "latency": "submit -> fetch return (host wall clock)",
+            "hbm_budget_bytes": budget, "peak_used_bytes": st_all["used_bytes"]}
+
+
+def run_serving(args):
+    """The serving mix of the default line at full length (config: 10 minutes)."""
+    import paper_2103_15418_b300 as lpf
+    res = serve_mix(lpf, seconds=args.seconds, cadence=args.cadence, jitter=args.jitter)
+    res["metric"] = METRIC
+    print(json.dumps(res), flush=True)
 
 
 def run_subband(args):
@@ -470,59 +703,6 @@ def run_subband(args):
         "steps": args.steps, "ms_per_step": 1e3 * elapsed / args.steps,
         "kernel_ms_per_step": per_push, "candidates_per_step": float(np.mean(ncand)),
         "data": "synthetic (seeded AARTFAAC-shaped stream)"}), flush=True)
-
-
-def run_serving(args):
-    """Serving mix: 2048^2/16/501, 1024^2/16/251 and 2 x 512^2/8/128 FP16 streams, frames
-    submitted at the cadence with +-5% jitter; p50/p99 submit -> finish latency and the
-    aggregate pixel*DM-trials/s of the finished frames."""
-    import threading
-    import torch
-    import paper_2103_15418_b300 as lpf
-    specs = synth.spec_serving_mix()
-    pools = []
-    for i, sp in enumerate(specs):
-        st = synth.SyntheticStream(sp, seed=60 + i)
-        pools.append([st.frame(t) for t in range(4)])
-    budget = 80 << 30
-    n = args.frames
-    jit = np.random.default_rng(7)
-    with lpf.Server(budget, max_streams=8) as srv:
-        ids = [srv.open_stream(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth, kappa=sp.kappa,
-                               box_r=sp.box_r, dtype=sp.dtype) for sp in specs]
-        counts = {i: 0 for i in ids}
-
-        def drain(i):
-            while counts[i] < n:
-                srv.fetch(i, timeout_ms=600000)
-                counts[i] += 1
-        threads = [threading.Thread(target=drain, args=(i,)) for i in ids]
-        for th in threads:
-            th.start()
-        t0 = time.perf_counter()
-        # staggered, jittered arrivals: stream k's frame T is due at (T + k/4) * cadence +- 5%
-        events = sorted((T + k / len(ids) + jit.uniform(-0.05, 0.05)) * args.cadence for T in range(n)
-                        for k in range(len(ids)))
-        order = sorted(((T + k / len(ids)) * args.cadence, k, T) for T in range(n) for k in range(len(ids)))
-        for (due, k, T), ev in zip(order, events):
-            wait = t0 + ev - time.perf_counter()
-            if wait > 0:
-                time.sleep(wait)
-            while srv.submit(ids[k], pools[k][T % 4], T) == lpf.LPF_E_BUSY:
-                time.sleep(0.0005)
-        for th in threads:
-            th.join()
-        wall = time.perf_counter() - t0
-        stats = srv.stats()
-        per = {specs[i].name: srv.stats(ids[i]) for i in range(len(ids))}
-    pixdm = sum(sp.H * sp.W * sp.n_dm for sp in specs) * n
-    line = {"metric": METRIC, "workload": "serving-mix-4-streams-fp16", "cadence_s": args.cadence,
-            "frames_per_stream": n, "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"],
-            "max_ms": stats["max_ms"], "pixel_dm_per_s_served": stats["pixel_dm_per_s"],
-            "offered_pixel_dm_per_s": pixdm / wall,
-            "per_stream_p99_ms": {k: v["p99_ms"] for k, v in per.items()},
-            "hbm_budget_bytes": budget, "peak_used_bytes": stats["used_bytes"]}
-    print(json.dumps(line), flush=True)
 
 
 def run_stress(args):

@@ -233,14 +233,16 @@ int lpf_extract_dynspec(lpf_stream* s, const lpf_candidate* c_host, int n, int T
  * stages the records in a fixed array in device global memory instead and
  * calls no allocating routine (no cudaMalloc, cudaFree or library allocator).
  *
- * Limits and sharing: at most LPF_STATIC_DYNSPEC_MAX candidates per call
- * (LPF_E_CAPACITY above that).  The array (LPF_STATIC_DYNSPEC_MAX records of
+ * Limits and sharing: at most LPF_STATIC_DYNSPEC_MAX candidates per call.
+ * Errors are those of lpf_extract_dynspec, checked in the same order, and
+ * then LPF_E_CAPACITY for a request above that maximum.  The array (LPF_STATIC_DYNSPEC_MAX records of
  * 24 bytes, 1.5 MiB) is part of the library image: every GPU that loads the
  * library holds it until the process exits.  All calls on a device share it,
  * so calls that overlap on the GPU race; issue them one at a time (from any
- * handle or thread).  Each call writes the records it reads and synchronises
- * the stream before returning, so nothing carries over between calls and the
- * next call may start as soon as this one returns.  The first call on each
+ * handle or thread).  Each call writes the records it reads and blocks until
+ * its gather has finished (it synchronises the stream's CUDA stream before
+ * returning), so nothing carries over between calls and the next call may
+ * start as soon as this one returns.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress, with that
  * device current); make that first call before any stream capture.
  */

@@ -29,7 +29,7 @@ method, each citing the passage of Ruhe et al. (arXiv 2103.15418) it follows:
                    (Welford) and scores zeta; bands over either threshold are
                    imputed with zeros
 
-Readings where the paper is silent or garbled (all listed in the design doc):
+Readings where the paper is silent or garbled (Sec. 2.1.1-2.1.2, Sec. 3.2, App. A):
   * C_DM = 4.148808e3 s MHz^2 cm^3 / pc (the printed unit "ms" is garbled; with
     nu in MHz the delay is in seconds); nu_ref = the highest frequency, so every
     delay is >= 0; delays are rounded half up, floor(x + 0.5), in FP64.

@@ -1349,16 +1349,17 @@ void launch_dynspec_records(lpf_stream* s, const lpf::CandidateRec* rec, int n, 
 
 extern "C" int lpf_extract_dynspec_static(lpf_stream* s, const lpf_candidate* c_host, int n, int Tw,
                                           float* out_dev) {
+    // the checks of lpf_extract_dynspec, in its order; the capacity last
     if (!s || n < 0 || Tw < 1 || (n > 0 && (!c_host || !out_dev))) return LPF_E_ARG;
-    if (n > LPF_STATIC_DYNSPEC_MAX) return LPF_E_CAPACITY;
     if (Tw > s->depth) return LPF_E_DEPTH;
     if (!s->polled) return LPF_E_NODATA;
     const int64_t T = s->polled_T;
     if (T - Tw + 1 < s->T_first) return LPF_E_STALE;
     if (s->last_T - s->depth + 1 > T - Tw + 1) return LPF_E_STALE;
+    if (n == 0) return LPF_OK;
     for (int i = 0; i < n; ++i)
         if (c_host[i].y < 0 || c_host[i].y >= s->H || c_host[i].x < 0 || c_host[i].x >= s->W) return LPF_E_ARG;
-    if (n == 0) return LPF_OK;
+    if (n > LPF_STATIC_DYNSPEC_MAX) return LPF_E_CAPACITY;
     if (cudaSetDevice(s->dev) != cudaSuccess) return LPF_E_CUDA;
     lpf::CandidateRec* rec = nullptr;
     int rc = records_on_device(s->dev, &rec);

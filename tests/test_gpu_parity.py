@@ -4,7 +4,7 @@ import pytest
 
 import synth
 from oracle import lpf_oracle as O
-from tests.parity import assert_sorted_unique, cached_frames, cached_residuals, compare_push
+from tests.parity import assert_sorted_unique, cached_frames, cached_residuals, compare_push, compare_storage
 
 pytestmark = pytest.mark.gpu
 
@@ -56,8 +56,8 @@ def test_aartfaac_bands_256px(lib, dtype):
             assert Tp == T and not trunc
             if T in checks:
                 assert_sorted_unique(c)
-                res = compare_push(c, fa, T, delays, spec.box_r, spec.kappa, gpu_stats=s.stats(),
-                                   res_at=ra)
+                res = compare_storage(c, fa, T, delays, spec.box_r, spec.kappa, dtype, gpu_stats=s.stats(),
+                                      res_at=ra)
                 assert res["matched"] > 0
 
 
@@ -99,7 +99,8 @@ def test_more_than_16_subbands(lib, F, dtype):
             assert not trunc
             if T >= delays.max():
                 assert_sorted_unique(c)
-                res = compare_push(c, fa, T, delays, spec.box_r, spec.kappa, gpu_stats=s.stats(), res_at=ra)
+                res = compare_storage(c, fa, T, delays, spec.box_r, spec.kappa, dtype, gpu_stats=s.stats(),
+                                      res_at=ra)
                 matched += res["matched"]
     assert matched > 0
 

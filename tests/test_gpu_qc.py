@@ -6,7 +6,7 @@ import pytest
 
 import synth
 from oracle import lpf_oracle as O
-from tests.parity import assert_sorted_unique, compare_push
+from tests.parity import assert_sorted_unique, compare_storage
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -59,7 +59,7 @@ def test_quality_control_matches_oracle(lib, dtype):
             assert np.allclose(z[fin], z_ref[T][fin], rtol=1e-4, atol=1e-3), T
             if T in (33, 37, 43):               # windows holding the imputed bands
                 assert_sorted_unique(c)
-                compare_push(c, fa, T, delays, spec.box_r, spec.kappa, gpu_stats=s.stats(), res_at=ra)
+                compare_storage(c, fa, T, delays, spec.box_r, spec.kappa, dtype, gpu_stats=s.stats(), res_at=ra)
 
 
 def test_quality_control_off_leaves_frames_untouched(lib):

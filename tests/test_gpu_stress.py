@@ -11,13 +11,15 @@ import pytest
 
 import synth
 from oracle import lpf_oracle as O
-from tests.parity import assert_sorted_unique, compare_push
+import json
+
+from tests.parity import SNR_RTOL, assert_sorted_unique, compare_storage, precision_vs_unrounded
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def test_stress_sampled_trials_and_dynspec(lib):
+def test_stress_sampled_trials_and_dynspec(lib, capsys):
     spec = synth.spec_stress(depth=114)
     st = synth.SyntheticStream(spec, seed=50)
     pool = [st.frame(t) for t in range(12)]
@@ -36,8 +38,14 @@ def test_stress_sampled_trials_and_dynspec(lib):
             _, c, n, trunc = s.poll(timeout_ms=120000)
         assert not trunc
         assert_sorted_unique(c)
-        compare_push(c, frame_at, T, delays, spec.box_r, spec.kappa, dms=[0, 1, 400, 1000],
-                     gpu_stats=s.stats(), res_at=res_at)
+        dms = [0, 1, 400, 1000]
+        compare_storage(c, frame_at, T, delays, spec.box_r, spec.kappa, "fp16", dms=dms,
+                        gpu_stats=s.stats(), res_at=res_at)
+        # precision report against the oracle on the unrounded frames
+        rep = precision_vs_unrounded(c, lambda t: pool[t % 12], T, delays, spec.box_r, spec.kappa, dms, "fp16")
+        with capsys.disabled():
+            print("\nPRECISION_REPORT " + json.dumps({"stress-2048x2048-32sb-1001dm-depth114": {"fp16": rep}}))
+        assert rep["sym_diff"] == 0 and rep["max_rel_snr_err"] <= SNR_RTOL["fp16"], rep
         Tw = 64
         ds = s.dynspec(c, Tw)                              # contiguous [n][32][64] FP32 batch
         assert ds.shape == (len(c), 32, Tw) and ds.is_contiguous()

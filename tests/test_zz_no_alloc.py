@@ -8,7 +8,8 @@ lpf_extract_dynspec_static stages the candidates in a fixed array compiled
 into the library instead.  This test calls it through the C ABI and checks it
 against lpf_extract_dynspec on two calls in a row (the second smaller than the
 first, so nothing left in the shared array from the first call may show), with
-the exact equality the other gather tests use, plus its capacity error.
+the exact equality the other gather tests use, plus its errors: capacity, an
+out-of-image pixel, and an oversized request before the first poll.
 The file is named to be collected last.
 """
 import ctypes
@@ -35,6 +36,14 @@ def test_static_gather_matches_allocating_gather(lib, dtype, box):
     st = synth.SyntheticStream(spec, seed=21)
     fn = _static_gather(lib)
     Tw = 12
+    big = np.zeros(lib.LPF_STATIC_DYNSPEC_MAX + 1, dtype=lib.CANDIDATE_DTYPE)
+    with lib.Stream(spec.H, spec.W, spec.freqs_mhz, spec.dm_grid, spec.depth, kappa=spec.kappa,
+                    box_r=spec.box_r, dtype=dtype) as s0:
+        # before the first poll an oversized request fails as the allocating gather
+        # would (no frame polled), ahead of the capacity check
+        out = torch.empty((len(big), spec.F, 1), device="cuda")
+        assert fn(s0._h, big.ctypes.data, len(big), 1, out.data_ptr()) == lib.LPF_E_NODATA
+        del out
     with lib.Stream(spec.H, spec.W, spec.freqs_mhz, spec.dm_grid, spec.depth, kappa=spec.kappa,
                     box_r=spec.box_r, dtype=dtype, dyn_box_r=box) as s:
         for T in range(20):
@@ -55,7 +64,6 @@ def test_static_gather_matches_allocating_gather(lib, dtype, box):
             torch.cuda.synchronize()
             assert torch.equal(out, ref)
         # more records than the fixed array holds: rejected before any copy
-        big = np.zeros(lib.LPF_STATIC_DYNSPEC_MAX + 1, dtype=lib.CANDIDATE_DTYPE)
         out = torch.empty((len(big), spec.F, 1), device="cuda")
         assert fn(s._h, big.ctypes.data, len(big), 1, out.data_ptr()) == lib.LPF_E_CAPACITY
         # an out-of-image pixel is an argument error, as for the allocating gather
