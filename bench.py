@@ -565,10 +565,9 @@ def run_ours(args):
 
 def launches_per_push(spec, qc):
     """Kernels of one push: residuals, counter reset, shift-sum, ring write, filter,
-    3x3 pass, 3 per ordering pass, formatting, statistics (+ 2 with quality control)."""
-    bits = lambda v: max(1, int(np.ceil(np.log2(v))))
-    passes = (bits(spec.W) + bits(spec.H) + bits(spec.n_dm) + 7) // 8
-    return 8 + 3 * passes + (2 if qc else 0)
+    3x3 pass, 4 ordering kernels (count, scan, scatter, sort + format), statistics
+    (+ 2 with quality control)."""
+    return 11 + (2 if qc else 0)
 
 
 # ---------------------------------------------------------------------------

@@ -100,13 +100,16 @@ typedef struct {
      * lpf_stream_open are then ignored (0 and NULL allowed); a candidate's dm_idx
      * is its band f and t0 its frame T; lpf_get_stats has one row per band.     */
     int    mode;          /* LPF_MODE_DISPERSED / LPF_MODE_SUBBAND                 default DISPERSED */
-    /* Per-subband detector only: iterated sigma clipping (Sec. 2.1.1).  Each
-     * iteration re-estimates C and S from the window pixels not yet flagged and
-     * adds the pixels over the threshold to the flags, until an iteration flags
-     * nothing new or clip_iters iterations; candidates are the flagged (2 lmax_r
-     * + 1)^2 maxima of X_f, with the S/N of the last iteration.  1 = one pass
-     * (the residual filter).                                                    */
-    int    clip_iters;    /* 1..16 (> 1 only with LPF_MODE_SUBBAND)                default 1 */
+    /* Iterated sigma clipping (Sec. 2.1.1).  Each iteration re-estimates C and S
+     * from the window pixels not yet flagged and adds the pixels over the
+     * threshold to the flags, until an iteration flags nothing new or clip_iters
+     * iterations; candidates are the flagged (2 lmax_r + 1)^2 maxima, with the
+     * S/N of the last iteration.  Per-subband detector: of the band images X_f.
+     * Dispersed search: of the dedispersed image D_d of every trial, on the
+     * direct-form path (D summed from the raw ring per distinct delay row, then
+     * the clipping passes over all rows; filter_impl 2 is refused).  1 = one
+     * pass.                                                                     */
+    int    clip_iters;    /* 1..16                                                 default 1 */
     /* Per-subband detector only: the Gaussian kernel of Sec. 2.1.1 instead of the
      * uniform box, truncated to the (2 box_r + 1)^2 window (box_r 1..16) and
      * normalised per pixel by its weight over the in-image (and, when clipping,
@@ -152,7 +155,7 @@ void lpf_default_params(lpf_params* p);
  * for the mode, bad dtype, non-positive frequency or cadence, negative DM, filter_impl 2 with another
  * box_r; an unknown mode or kernel; the Gaussian kernel outside the per-subband detector or with
  * gauss_sigma not positive and finite; the per-subband detector with the box and box_r other than 7 or
- * 15, or with filter_impl 1; clip_iters outside 1..16, or above 1 outside the per-subband detector;
+ * 15, or with filter_impl 1; clip_iters outside 1..16, or above 1 in the dispersed search with filter_impl 2;
  * quality-control thresholds not positive or qc_min_frames < 2), LPF_E_DEPTH (buffer_depth < max delay
  * + 1), LPF_E_OOM, LPF_E_CUDA (no device).
  */

@@ -8,7 +8,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblpf.so")
 SOURCES = ["lpf_stream.cu", "lpf_server.cpp"]
 HEADERS = ["lpf_kernels.cuh", "lpf_dedisperse.cuh", "lpf_residual.cuh", "lpf_filter_res.cuh",
-           "lpf_filter_stream.cuh", "lpf_qc.cuh", "lpf_clip.cuh", os.path.join("..", "..", "include", "lpf.h")]
+           "lpf_filter_stream.cuh", "lpf_qc.cuh", "lpf_clip.cuh", "lpf_order.cuh", os.path.join("..", "..", "include", "lpf.h")]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",

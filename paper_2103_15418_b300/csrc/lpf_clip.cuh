@@ -1,5 +1,7 @@
-// Iterated sigma clipping of the per-subband detector (Sec. 2.1.1): at each
-// iteration the local centre C and spread S of a band image X are the
+// Iterated sigma clipping (Sec. 2.1.1) of the per-subband detector's band
+// images, or of the dispersed search's D images (one per distinct delay row, on
+// the direct-form path): at each iteration the local centre C and spread S of an
+// image X are the
 // kernel-weighted means over the window pixels not yet flagged (normalised by
 // their kernel weight n), and the pixels with (X - C) / sqrt(S) > kappa join the
 // flags; the loop stops when an iteration flags nothing new (each launch of a
@@ -297,11 +299,13 @@ __global__ void __launch_bounds__(256) k_clip_flag(ClipArgs c, int it) {
     if (__syncthreads_or(fresh) && threadIdx.x == 0) atomicOr(c.changed + it, 1u);
 }
 
-// Grid (blocks per band, F): S/N of the last iteration, the per-band statistics
-// partials (FP32 per thread, FP64 per block), and the candidates: flagged pixels
-// with S > 0 that are (2k+1)^2 maxima of X, one record each (band f = trial f).
+// Grid (blocks per plane, planes): S/N of the last iteration, the per-plane
+// statistics partials (FP32 per thread, FP64 per block), and the candidates:
+// flagged pixels with S > 0 that are (2k+1)^2 maxima of X, one record per trial
+// of the plane's row (a band: one trial; a distinct delay row: its members).
 __global__ void __launch_bounds__(256) k_clip_emit(ClipArgs c, FilterArgs a, int k) {
     const int f = blockIdx.y;
+    const int m0 = a.member_start[f], nm = a.member_start[f + 1] - m0;
     const int64_t HW = (int64_t)c.H * c.W, plane = (int64_t)f * c.P;
     const int lane = threadIdx.x & 31;
     float s1 = 0.f, s2 = 0.f, cnt = 0.f;
@@ -338,13 +342,17 @@ __global__ void __launch_bounds__(256) k_clip_emit(ClipArgs c, FilterArgs a, int
             if (bal) {
                 unsigned b0 = 0;
                 const int leader = __ffs(bal) - 1;
-                if (lane == leader) b0 = atomicAdd(a.counter, (unsigned)__popc(bal));
+                if (lane == leader) b0 = atomicAdd(a.counter, (unsigned)(__popc(bal) * nm));
                 b0 = __shfl_sync(0xffffffffu, b0, leader);
                 if (cand) {
-                    const unsigned idx = b0 + __popc(bal & ((1u << lane) - 1u));
-                    if (idx < (unsigned)a.cap) {
-                        a.keys[idx] = ((uint64_t)a.member_ord[f] << (a.bx + a.by)) | ((uint64_t)y << a.bx) | (uint64_t)x;
-                        a.vals[idx] = snr;
+                    const unsigned base = b0 + __popc(bal & ((1u << lane) - 1u)) * (unsigned)nm;
+                    const uint64_t pix = ((uint64_t)y << a.bx) | (uint64_t)x;
+                    for (int m = 0; m < nm; ++m) {
+                        const unsigned idx = base + (unsigned)m;
+                        if (idx < (unsigned)a.cap) {
+                            a.keys[idx] = ((uint64_t)a.member_ord[m0 + m] << (a.bx + a.by)) | pix;
+                            a.vals[idx] = snr;
+                        }
                     }
                 }
             }

@@ -16,8 +16,7 @@ namespace lpf {
 
 constexpr int kTile = 64;             // output tile of the filter kernel (pixels per side)
 constexpr int kFilterThreads = 256;
-constexpr int kSortThreads = 256;
-constexpr int kSortBlocks = 148;      // blocks of the radix-sort passes
+constexpr int kSortBlocks = 148;      // blocks of the candidate-ordering passes
 
 // ------------------------------------------------------------------ storage I/O
 __device__ __forceinline__ float4 ld4(const float* p) {
@@ -349,157 +348,12 @@ __global__ void k_stats(const double* __restrict__ partials, int n_tiles, double
         for (int k = 0; k < 3; ++k) stats[row * 3 + k] = red[k][0];
 }
 
-// ------------------------------------------------------------------ candidate ordering
-// Stable LSD radix sort of (u64 key, f32 value) records, 8 bits per pass.  The
-// record count n = min(*n_ptr, cap) lives on the device; each of the nb blocks
-// owns a contiguous chunk, so the grid does not depend on n.
-__device__ __forceinline__ void chunk_of(unsigned n, int nb, int b, unsigned& lo, unsigned& hi) {
-    unsigned chunk = (n + nb - 1) / nb;
-    lo = min(n, (unsigned)b * chunk);
-    hi = min(n, lo + chunk);
-}
-
-__global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint64_t* __restrict__ keys,
-                                                          const unsigned* __restrict__ n_ptr,
-                                                          int cap, int shift,
-                                                          unsigned* __restrict__ hist) {
-    __shared__ unsigned h[256];
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    unsigned n = min(*n_ptr, (unsigned)cap), lo, hi;
-    chunk_of(n, gridDim.x, blockIdx.x, lo, hi);
-    for (unsigned i = lo + threadIdx.x; i < hi; i += blockDim.x)
-        atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
-    __syncthreads();
-    hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
-}
-
-// Exclusive scan of hist[256 * nb] (digit-major), one block of 1024 threads:
-// warp w owns digits 8w .. 8w+7; it loads their nb block counts at once
-// (coalesced, nb <= 160), scans each digit with warp shuffles, and after the
-// 256 digit totals are scanned adds the digit offset on the way back.
-static_assert(kSortBlocks <= 160, "scan holds 5 chunks of 32 block counts per digit");
-__global__ void __launch_bounds__(1024) k_rs_scan(unsigned* __restrict__ hist, int nb) {
-    __shared__ unsigned tot[256];
-    __shared__ unsigned base[256];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        unsigned v[4][5];
-#pragma unroll
-        for (int dd = 0; dd < 4; ++dd)
-#pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                const int i = c * 32 + lane;
-                v[dd][c] = i < nb ? hist[(warp * 8 + 4 * half + dd) * nb + i] : 0u;
-            }
-#pragma unroll
-        for (int dd = 0; dd < 4; ++dd) {
-            const int d = warp * 8 + 4 * half + dd;
-            unsigned run = 0;
-#pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                unsigned inc = v[dd][c];
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    unsigned u = __shfl_up_sync(0xffffffffu, inc, o);
-                    if (lane >= o) inc += u;
-                }
-                const int i = c * 32 + lane;
-                if (i < nb) hist[d * nb + i] = run + inc - v[dd][c];
-                run += __shfl_sync(0xffffffffu, inc, 31);
-            }
-            if (lane == 0) tot[d] = run;
-        }
-    }
-    __syncthreads();
-    if (warp == 0) {
-        unsigned w8[8], sum = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) { w8[k] = tot[lane * 8 + k]; sum += w8[k]; }
-        unsigned inc = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned u = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += u;
-        }
-        unsigned run = inc - sum;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) { base[lane * 8 + k] = run; run += w8[k]; }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int dd = 0; dd < 8; ++dd)
-#pragma unroll
-        for (int c = 0; c < 5; ++c) {
-            const int i = c * 32 + lane;
-            if (i < nb) hist[(warp * 8 + dd) * nb + i] += base[warp * 8 + dd];
-        }
-}
-
-__global__ void __launch_bounds__(kSortThreads) k_rs_scatter(
-    const uint64_t* __restrict__ kin, const float* __restrict__ vin, uint64_t* __restrict__ kout,
-    float* __restrict__ vout, const unsigned* __restrict__ n_ptr, int cap, int shift,
-    const unsigned* __restrict__ hist) {
-    __shared__ unsigned base[256];
-    __shared__ unsigned wcnt[kSortThreads / 32][256];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    unsigned n = min(*n_ptr, (unsigned)cap), lo, hi;
-    chunk_of(n, gridDim.x, blockIdx.x, lo, hi);
-    base[t] = hist[t * gridDim.x + blockIdx.x];
-    for (unsigned tile = lo; tile < hi; tile += kSortThreads) {
-#pragma unroll
-        for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][t] = 0;
-        __syncthreads();
-        unsigned i = tile + t;
-        bool valid = i < hi;
-        uint64_t key = valid ? kin[i] : 0;
-        unsigned digit = valid ? (unsigned)((key >> shift) & 255u) : 256u;
-        unsigned peers = __match_any_sync(0xffffffffu, digit);
-        unsigned rank = __popc(peers & ((1u << lane) - 1u));
-        if (valid && rank == 0) wcnt[warp][digit] = __popc(peers);
-        __syncthreads();
-        if (valid) {
-            unsigned off = base[digit] + rank;
-            for (int w = 0; w < warp; ++w) off += wcnt[w][digit];
-            kout[off] = key;
-            vout[off] = vin[i];
-        }
-        __syncthreads();
-        unsigned tot = 0;
-#pragma unroll
-        for (int w = 0; w < kSortThreads / 32; ++w) tot += wcnt[w][t];
-        base[t] += tot;
-        __syncthreads();
-    }
-}
-
 // ------------------------------------------------------------------ output records
 struct CandidateRec {   // mirrors lpf_candidate (24 bytes)
     int64_t t0;
     int32_t dm_idx, y, x;
     float snr;
 };
-
-__global__ void k_format(const uint64_t* __restrict__ keys, const float* __restrict__ vals,
-                         const unsigned* __restrict__ n_ptr, int cap,
-                         CandidateRec* __restrict__ out, const int* __restrict__ ord2d,
-                         const int* __restrict__ dmax_of_d, int64_t T, int bx, int by) {
-    unsigned n = min(*n_ptr, (unsigned)cap);
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        uint64_t k = keys[i];
-        int x = (int)(k & ((1ull << bx) - 1));
-        int y = (int)((k >> bx) & ((1ull << by) - 1));
-        int d = ord2d[(int)(k >> (bx + by))];
-        CandidateRec c;
-        c.t0 = T - dmax_of_d[d];
-        c.dm_idx = d;
-        c.y = y;
-        c.x = x;
-        c.snr = vals[i];
-        out[i] = c;
-    }
-}
 
 __global__ void k_zero_u32(unsigned* p, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -13,6 +13,7 @@
 #include "lpf_filter_res.cuh"
 #include "lpf_qc.cuh"
 #include "lpf_clip.cuh"
+#include "lpf_order.cuh"
 
 #include <algorithm>
 #include <chrono>
@@ -52,7 +53,7 @@ struct PushLane {
     uint64_t* keys[2] = {nullptr, nullptr};
     float* vals[2] = {nullptr, nullptr};
     unsigned* counter = nullptr;       // [4]: candidates, -, crossings (u64 at word 2)
-    unsigned* hist = nullptr;          // radix-sort block histograms
+    unsigned* ord = nullptr;           // [3][n ranks]: records per trial rank, bucket starts, cursors
     double* partials = nullptr;        // [n_distinct][filter blocks][3]
     cudaEvent_t filter_done = nullptr; // the push's filter finished: its tail may start
     cudaEvent_t lmax_done = nullptr;   // the push's 3x3 pass finished: the raw ring slot it
@@ -132,8 +133,9 @@ struct lpf_stream {
     // clipping path of the per-subband detector (clip_iters > 1 or the Gaussian kernel)
     bool clip = false;
     float* clip_w = nullptr;         // [box_r + 1] kernel factors g(|d|) (1 for the box)
-    uint8_t* clip_flags = nullptr;   // [F][P]
-    float* clip_planes = nullptr;    // T1, T2, C, N, S: 5 x [F][P]
+    int clip_planes_n = 0;           // planes clipped per push: F (per-subband) or n_distinct (dispersed)
+    uint8_t* clip_flags = nullptr;   // [clip_planes_n][P]
+    float* clip_planes = nullptr;    // T1, T2, C, N, S: 5 x [clip_planes_n][P]
     unsigned* clip_changed = nullptr;  // [clip_iters]
     int64_t last_qc_T = -1;
     double* h_stats = nullptr;       // [slots][n_distinct][3]
@@ -202,7 +204,7 @@ void free_all(lpf_stream* s) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& L : s->lanes) {
-        void* lp[] = {L.keys[0], L.keys[1], L.vals[0], L.vals[1], L.counter, L.hist, L.partials};
+        void* lp[] = {L.keys[0], L.keys[1], L.vals[0], L.vals[1], L.counter, L.ord, L.partials};
         for (void* p : lp)
             if (p) cudaFree(p);
         if (L.filter_done) cudaEventDestroy(L.filter_done);
@@ -583,45 +585,64 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
     const float* filter_images = s->D;
     lpf::ClipArgs ca{};
     if (clip) {
-        const int64_t n = (int64_t)s->F * s->P;
+        // planes clipped: the F band images of the newest frame (per-subband
+        // detector), or the D images of the active distinct delay rows (dispersed
+        // search, direct form: the shift-sum of the raw ring)
+        const bool band = s->prm.mode == LPF_MODE_SUBBAND;
+        const int np = band ? s->F : n_rows;
+        const int64_t ns = (int64_t)s->clip_planes_n * s->P;   // stride of the scratch plane sets
         ca.X = s->D;
         ca.flags = s->clip_flags;
         ca.T1 = s->clip_planes;
-        ca.T2 = ca.T1 + n;
-        ca.C = ca.T2 + n;
-        ca.N = ca.C + n;
-        ca.S = ca.N + n;
+        ca.T2 = ca.T1 + ns;
+        ca.C = ca.T2 + ns;
+        ca.N = ca.C + ns;
+        ca.S = ca.N + ns;
         ca.changed = s->clip_changed;
         ca.w = s->clip_w;
-        ca.F = s->F; ca.H = s->H; ca.W = s->W; ca.r = s->prm.box_r; ca.P = s->P; ca.kappa = s->prm.kappa;
-        const int g = 148 * 8;
-        lpf::k_zero_u32<<<1, 32, 0, s->st>>>(s->clip_changed, s->prm.clip_iters);
-        switch (s->prm.dtype) {
-            case LPF_FP32:
-                lpf::k_clip_init<float><<<g, 256, 0, s->st>>>(ca, reinterpret_cast<const float*>(s->ring) + ring_slot * n);
-                break;
-            case LPF_FP16:
-                lpf::k_clip_init<__half><<<g, 256, 0, s->st>>>(ca, reinterpret_cast<const __half*>(s->ring) + ring_slot * n);
-                break;
-            default:
-                lpf::k_clip_init<__nv_bfloat16><<<g, 256, 0, s->st>>>(
-                    ca, reinterpret_cast<const __nv_bfloat16*>(s->ring) + ring_slot * n);
-                break;
-        }
-        // window sums: shared-memory tiles, the radius a compile-time constant
-        const dim3 gh((unsigned)(((s->W + lpf::kClipHX - 1) / lpf::kClipHX) * s->H), (unsigned)s->F);
-        const dim3 gv((unsigned)((s->W + lpf::kClipVX - 1) / lpf::kClipVX),
-                      (unsigned)((s->H + lpf::kClipVY - 1) / lpf::kClipVY), (unsigned)s->F);
-        for (int it = 0; it < s->prm.clip_iters; ++it) {
-            lpf::with_radius(ca.r, [&](auto rc) {
-                constexpr int R = decltype(rc)::value;
-                lpf::k_clip_hsum<R, 0><<<gh, 128, 0, s->st>>>(ca, it);
-                lpf::k_clip_vsum<R, 0><<<gv, 128, 0, s->st>>>(ca, it);
-                lpf::k_clip_hsum<R, 1><<<gh, 128, 0, s->st>>>(ca, it);
-                lpf::k_clip_vsum<R, 1><<<gv, 128, 0, s->st>>>(ca, it);
-            });
-            lpf::k_clip_flag<<<dim3((unsigned)std::min<int64_t>((s->HW + 1023) / 1024, 65535), (unsigned)s->F), 256,
-                                0, s->st>>>(ca, it);
+        ca.F = np; ca.H = s->H; ca.W = s->W; ca.r = s->prm.box_r; ca.P = s->P; ca.kappa = s->prm.kappa;
+        if (np > 0) {
+            const int g = 148 * 8;
+            const int64_t n = (int64_t)s->F * s->P;             // one ring slot
+            lpf::k_zero_u32<<<1, 32, 0, s->st>>>(s->clip_changed, s->prm.clip_iters);
+            if (band) {
+                switch (s->prm.dtype) {
+                    case LPF_FP32:
+                        lpf::k_clip_init<float><<<g, 256, 0, s->st>>>(
+                            ca, reinterpret_cast<const float*>(s->ring) + ring_slot * n);
+                        break;
+                    case LPF_FP16:
+                        lpf::k_clip_init<__half><<<g, 256, 0, s->st>>>(
+                            ca, reinterpret_cast<const __half*>(s->ring) + ring_slot * n);
+                        break;
+                    default:
+                        lpf::k_clip_init<__nv_bfloat16><<<g, 256, 0, s->st>>>(
+                            ca, reinterpret_cast<const __nv_bfloat16*>(s->ring) + ring_slot * n);
+                        break;
+                }
+            } else {
+                switch (s->prm.dtype) {
+                    case LPF_FP32: launch_dedisperse<float>(s, n_rows, Tmod); break;
+                    case LPF_FP16: launch_dedisperse<__half>(s, n_rows, Tmod); break;
+                    default: launch_dedisperse<__nv_bfloat16>(s, n_rows, Tmod); break;
+                }
+                LPF_TRY(cudaMemsetAsync(s->clip_flags, 0, (size_t)np * s->P, s->st));
+            }
+            // window sums: shared-memory tiles, the radius a compile-time constant
+            const dim3 gh((unsigned)(((s->W + lpf::kClipHX - 1) / lpf::kClipHX) * s->H), (unsigned)np);
+            const dim3 gv((unsigned)((s->W + lpf::kClipVX - 1) / lpf::kClipVX),
+                          (unsigned)((s->H + lpf::kClipVY - 1) / lpf::kClipVY), (unsigned)np);
+            for (int it = 0; it < s->prm.clip_iters; ++it) {
+                lpf::with_radius(ca.r, [&](auto rc) {
+                    constexpr int R = decltype(rc)::value;
+                    lpf::k_clip_hsum<R, 0><<<gh, 128, 0, s->st>>>(ca, it);
+                    lpf::k_clip_vsum<R, 0><<<gv, 128, 0, s->st>>>(ca, it);
+                    lpf::k_clip_hsum<R, 1><<<gh, 128, 0, s->st>>>(ca, it);
+                    lpf::k_clip_vsum<R, 1><<<gv, 128, 0, s->st>>>(ca, it);
+                });
+                lpf::k_clip_flag<<<dim3((unsigned)std::min<int64_t>((s->HW + 1023) / 1024, 65535), (unsigned)np),
+                                    256, 0, s->st>>>(ca, it);
+            }
         }
     } else if (s->prm.mode == LPF_MODE_SUBBAND) {
         const int64_t n = (int64_t)s->F * s->P;
@@ -656,7 +677,7 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
         a.keys = L.keys[0]; a.vals = L.vals[0]; a.counter = L.counter; a.cap = s->prm.cand_cap;
         a.bx = s->bx; a.by = s->by; a.partials = L.partials;
         if (clip) {
-            lpf::k_clip_emit<<<dim3((unsigned)n_filter_blocks(s), (unsigned)s->F), 256, 0, s->st>>>(
+            lpf::k_clip_emit<<<dim3((unsigned)n_filter_blocks(s), (unsigned)ca.F), 256, 0, s->st>>>(
                 ca, a, s->prm.lmax_r);
         } else if (s->stream_filter) {
             switch (s->prm.dtype) {
@@ -689,18 +710,23 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
     }
     LPF_TRY(cudaEventRecord(L.lmax_done, ts));
     prof_mark(s, sl, ST_SORT, ts);
-    int cur = 0;
-    for (int shift = 0; shift < s->key_bits; shift += 8) {
-        lpf::k_rs_hist<<<kSortBlocks, lpf::kSortThreads, 0, ts>>>(L.keys[cur], L.counter, s->prm.cand_cap, shift,
-                                                                 L.hist);
-        lpf::k_rs_scan<<<1, 1024, 0, ts>>>(L.hist, kSortBlocks);
-        lpf::k_rs_scatter<<<kSortBlocks, lpf::kSortThreads, 0, ts>>>(
-            L.keys[cur], L.vals[cur], L.keys[cur ^ 1], L.vals[cur ^ 1], L.counter, s->prm.cand_cap, shift, L.hist);
-        cur ^= 1;
+    // ordering: counting sort on the trial rank, then each rank's bucket sorted by
+    // pixel and formatted (lpf_order.cuh)
+    {
+        const int shift = s->bx + s->by, n_ord = s->n_dm;
+        unsigned* counts = L.ord;
+        unsigned* start = L.ord + n_ord;
+        unsigned* cursor = L.ord + 2 * n_ord;
+        lpf::k_ord_count<<<kSortBlocks, lpf::kOrdThreads, 0, ts>>>(L.keys[0], L.counter, s->prm.cand_cap, shift,
+                                                                   n_ord, counts);
+        lpf::k_ord_scan<<<1, 1024, 0, ts>>>(counts, n_ord, start, cursor);
+        lpf::k_ord_scatter<<<kSortBlocks, lpf::kOrdThreads, 0, ts>>>(L.keys[0], L.vals[0], L.counter,
+                                                                     s->prm.cand_cap, shift, cursor, L.keys[1],
+                                                                     L.vals[1]);
+        prof_mark(s, sl, ST_FORMAT, ts);
+        lpf::k_ord_sort_format<<<std::min(n_ord, 148 * 8), lpf::kOrdThreads, lpf::ord_sort_smem_bytes(), ts>>>(
+            L.keys[1], L.vals[1], start, cursor, n_ord, slot.d_out, s->d_ord2d, s->d_dmax, T, s->bx, s->by);
     }
-    prof_mark(s, sl, ST_FORMAT, ts);
-    lpf::k_format<<<148 * 4, 256, 0, ts>>>(L.keys[cur], L.vals[cur], L.counter, s->prm.cand_cap, slot.d_out,
-                                           s->d_ord2d, s->d_dmax, T, s->bx, s->by);
     prof_mark(s, sl, ST_STATS, ts);
     if (n_rows > 0)
         lpf::k_stats<<<n_rows, 256, 0, ts>>>(L.partials, n_filter_blocks(s), slot.d_stats);
@@ -806,8 +832,10 @@ int plan_stream(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, 
     if (gauss && (!band || !(prm.gauss_sigma > 0) || !std::isfinite(prm.gauss_sigma))) return LPF_E_ARG;
     // the per-subband detector with the box runs on the residual planes: streaming filter only
     if (band && !gauss && (prm.filter_impl == 1 || (prm.box_r != 7 && prm.box_r != 15))) return LPF_E_ARG;
-    // iterated clipping: per-subband detector only (the dispersed search is one pass)
-    if (prm.clip_iters < 1 || prm.clip_iters > 16 || (!band && prm.clip_iters != 1)) return LPF_E_ARG;
+    // iterated clipping: the per-subband detector, or the dispersed search on the
+    // direct-form path (D itself per delay row; the box kernel)
+    if (prm.clip_iters < 1 || prm.clip_iters > 16) return LPF_E_ARG;
+    if (!band && prm.clip_iters > 1 && prm.filter_impl == 2) return LPF_E_ARG;
     if (prm.dtype < LPF_FP32 || prm.dtype > LPF_BF16 || prm.cand_cap < 1 || prm.dyn_box_r < 0) return LPF_E_ARG;
     if (prm.result_slots < 1 || prm.result_slots > kMaxSlots) return LPF_E_ARG;
     if (!std::isfinite(prm.kappa)) return LPF_E_ARG;
@@ -853,7 +881,9 @@ int plan_stream(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, 
     s->filter_smem = filter_smem_bytes(prm.box_r, s->filter_rmax);
     // the clipping path (per-subband detector, clip_iters > 1 or the Gaussian kernel)
     // sums its windows directly from the raw ring: no residual ring, no crossing list
-    s->clip = band && (prm.clip_iters > 1 || gauss);
+    s->clip = prm.clip_iters > 1 || gauss;
+    // clipping planes: one per band image (per-subband detector) or per distinct delay row
+    s->clip_planes_n = band ? F : s->n_distinct;
     s->stream_filter = !s->clip && (band || prm.filter_impl == 2 ||
                                     (prm.filter_impl == 0 && (prm.box_r == 7 || prm.box_r == 15)));
     s->n_strips = (W + lpf::kStreamTX - 1) / lpf::kStreamTX;
@@ -885,7 +915,8 @@ size_t footprint_bytes(const lpf_stream* s) {
     t += b(nd * s->P * 4) + b(2 * (size_t)s->F * s->HW * 4) + b(nd * s->F * 2) + b(nd * 4);
     if (s->xcap > 0) t += b((size_t)s->xcap * 8) + b((size_t)s->xcap * 4);
     if (s->clip)
-        t += b((size_t)s->F * s->P) + b(5 * (size_t)s->F * s->P * 4) + b((size_t)s->prm.clip_iters * 4) +
+        t += b((size_t)s->clip_planes_n * s->P) + b(5 * (size_t)s->clip_planes_n * s->P * 4) +
+             b((size_t)s->prm.clip_iters * 4) +
              b((size_t)(s->prm.box_r + 1) * 4);
     if (s->prm.qc) {
         t += 2 * b((size_t)s->F * s->P * 4) + b((size_t)s->F * 4) + b((size_t)s->F * 4) +
@@ -893,8 +924,8 @@ size_t footprint_bytes(const lpf_stream* s) {
         t += (size_t)s->n_slots * b(sizeof(lpf::QcRecord));
     }
     t += b(s->member_start.size() * 4) + b(s->member_ord.size() * 4) + 2 * b((size_t)s->n_dm * 4);
-    // two push lanes: keys and values (x2 for the sort), counter, histograms, partials
-    t += 2 * (2 * (b(cap * 8) + b(cap * 4)) + b(16) + b((size_t)256 * kSortBlocks * 4) +
+    // two push lanes: keys and values (x2 for the ordering), counter, rank buckets, partials
+    t += 2 * (2 * (b(cap * 8) + b(cap * 4)) + b(16) + b((size_t)3 * s->n_dm * 4) +
               b(nd * n_filter_blocks(s) * 3 * 8));
     t += (size_t)s->n_slots * (b(cap * sizeof(lpf::CandidateRec)) + b(nd * 3 * 8));
     return t;
@@ -979,7 +1010,9 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
             if (rc == LPF_OK) rc = dev_alloc(s, &L.vals[i], (size_t)prm.cand_cap);
         }
         if (rc == LPF_OK) rc = dev_alloc(s, &L.counter, 4);
-        if (rc == LPF_OK) rc = dev_alloc(s, &L.hist, (size_t)256 * kSortBlocks);
+        if (rc == LPF_OK) rc = dev_alloc(s, &L.ord, (size_t)3 * s->n_dm);
+        // the rank counts start at zero; the scan clears them after every push
+        if (rc == LPF_OK && cudaMemsetAsync(L.ord, 0, (size_t)3 * s->n_dm * 4, s->st) != cudaSuccess) rc = LPF_E_CUDA;
         if (rc == LPF_OK) rc = dev_alloc(s, &L.partials, (size_t)s->n_distinct * n_filter_blocks(s) * 3);
         if (rc == LPF_OK && (cudaEventCreateWithFlags(&L.filter_done, cudaEventDisableTiming) != cudaSuccess ||
                              cudaEventCreateWithFlags(&L.lmax_done, cudaEventDisableTiming) != cudaSuccess ||
@@ -1002,8 +1035,8 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
         if (rc == LPF_OK && cudaMemcpy(s->clip_w, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice) !=
                                 cudaSuccess)
             rc = LPF_E_CUDA;
-        if (rc == LPF_OK) rc = dev_alloc(s, &s->clip_flags, (size_t)F * s->P);
-        if (rc == LPF_OK) rc = dev_alloc(s, &s->clip_planes, 5 * (size_t)F * s->P);
+        if (rc == LPF_OK) rc = dev_alloc(s, &s->clip_flags, (size_t)s->clip_planes_n * s->P);
+        if (rc == LPF_OK) rc = dev_alloc(s, &s->clip_planes, 5 * (size_t)s->clip_planes_n * s->P);
         if (rc == LPF_OK) rc = dev_alloc(s, &s->clip_changed, (size_t)prm.clip_iters);
     }
     if (prm.qc) {

@@ -67,7 +67,7 @@ def test_argument_validation_before_any_cuda_call():
         dict(H=8, W=8, freqs_mhz=f, dm_grid=None, depth=2, mode="subband", lmax_r=4),
         dict(H=8, W=8, freqs_mhz=f, dm_grid=None, depth=2, mode="subband", box_r=5),
         dict(H=8, W=8, freqs_mhz=f, dm_grid=None, depth=2, mode="subband", filter_impl="tiled"),
-        dict(H=8, W=8, freqs_mhz=f, dm_grid=dm, depth=8, clip_iters=3),        # one pass for DM trials
+        dict(H=8, W=8, freqs_mhz=f, dm_grid=dm, depth=8, clip_iters=3, filter_impl="streaming"),  # direct form
         dict(H=8, W=8, freqs_mhz=f, dm_grid=None, depth=2, mode="subband", clip_iters=17),
         dict(H=8, W=8, freqs_mhz=f, dm_grid=dm, depth=8, kernel="gauss", gauss_sigma=2.0),  # subband only
         dict(H=8, W=8, freqs_mhz=f, dm_grid=None, depth=2, mode="subband", kernel="gauss"),  # s = 0
@@ -167,6 +167,19 @@ def test_clipping_footprint():
     # (+ the kernel factors and the statistics partials of the other block layout)
     assert delta <= many - one < delta + 65536
     assert delta <= gauss - one < delta + 65536
+
+
+def test_dispersed_clipping_footprint():
+    """Clipping in the dispersed search runs on the direct-form path: the tiled
+    path's buffers plus a flag plane and five FP32 planes per distinct delay row."""
+    import synth
+    from oracle import lpf_oracle as O
+    sp = synth.spec_aartfaac(H=256, W=256)
+    tiled = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth, filter_impl="tiled")
+    clip = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth, clip_iters=3)
+    rows = len({tuple(r) for r in O.delay_table(sp.freqs_mhz, sp.dm_grid, sp.cadence_s).tolist()})
+    delta = rows * sp.H * sp.W * 21
+    assert delta <= clip - tiled < delta + 65536
 
 
 def test_binding_refuses_buffers_the_library_would_overrun():
