@@ -3,9 +3,12 @@
 // One lpf_stream owns: the FP64-built integer delay table and its distinct-row
 // plan, the device ring buffer, the dedispersed-image scratch, the candidate
 // sort buffers and a small ring of result slots (pushed-but-unpolled frames).
-// Every push enqueues, on the stream's CUDA stream:
-//   ingest -> shift-sum -> filter/detect -> radix sort -> format -> stats
-// and records an event; poll waits on that event with a deadline.
+// Every push enqueues ingest -> shift-sum -> filter/detect -> 3x3 maximum ->
+// ordering -> stats and records an event; poll waits on that event with a
+// deadline.  On the residual path three CUDA streams carry a push: the main
+// stream (residuals, shift-sum, raw-ring write), a filter stream (the filter
+// of push T runs beside the residuals and shift-sum of push T + 1) and a tail
+// stream (3x3 maximum, ordering, statistics, result copies).
 #include "../../include/lpf.h"
 #include "lpf_kernels.cuh"
 #include "lpf_dedisperse.cuh"
@@ -32,6 +35,8 @@ namespace {
 constexpr double kCdmSeconds = 4.148808e3;   // s MHz^2 cm^3 / pc (Sec. 3.2)
 using lpf::kSortBlocks;
 constexpr int kMaxSlots = 16;
+constexpr int kLmaxEv = 16;            // ring of per-push events: the 3x3 pass of push n done
+constexpr int kSpareSlots = 2;         // raw/residual ring slots beyond the requested depth (residual path)
 
 // Stages in the order their marks are recorded.  The residual path writes the
 // raw ring after the shift-sum (ring_write); the tiled and clipping paths write
@@ -53,11 +58,13 @@ struct PushLane {
     uint64_t* keys[2] = {nullptr, nullptr};
     float* vals[2] = {nullptr, nullptr};
     unsigned* counter = nullptr;       // [4]: candidates, -, crossings (u64 at word 2)
+    uint64_t* xkeys = nullptr;         // threshold crossings of the residual path (row, y, x) ...
+    float* xvals = nullptr;            // ... and their S/N
     unsigned* ord = nullptr;           // [3][n ranks]: records per trial rank, bucket starts, cursors
     double* partials = nullptr;        // [n_distinct][filter blocks][3]
+    cudaEvent_t dd_done = nullptr;     // the push's shift-sum finished: its filter may start
+    cudaEvent_t rw_done = nullptr;     // the push's raw-ring write finished: its 3x3 pass may read the frame
     cudaEvent_t filter_done = nullptr; // the push's filter finished: its tail may start
-    cudaEvent_t lmax_done = nullptr;   // the push's 3x3 pass finished: the raw ring slot it
-                                       // reads last and the crossing list may be rewritten
     cudaEvent_t tail_done = nullptr;   // the push's tail finished: the lane may be reused
 };
 
@@ -75,6 +82,7 @@ struct Slot {
 struct lpf_stream {
     int dev = 0;
     int H = 0, W = 0, F = 0, n_dm = 0, depth = 0;
+    int ring_n = 0;                  // ring slots: depth (+ kSpareSlots on the residual path)
     lpf_params prm{};
     int64_t HW = 0, P = 0;
     size_t elem = 4;
@@ -94,9 +102,8 @@ struct lpf_stream {
     // device memory
     void* ring = nullptr;
     float* D = nullptr;
-    uint64_t* xkeys = nullptr;      // threshold crossings of the residual path (row, y, x) ...
-    float* xvals = nullptr;         // ... and their S/N
-    int64_t xcap = 0;               // crossing capacity
+    float* D2 = nullptr;            // second image buffer of the residual path (lane 1)
+    int64_t xcap = 0;               // crossing capacity (per lane)
     float* stage = nullptr;          // host-push staging frames [2][F][HW]
     cudaStream_t h2d_st = nullptr;   // uploads of host frames
     cudaEvent_t stage_ready[2] = {nullptr, nullptr};   // upload into stage i done
@@ -111,6 +118,8 @@ struct lpf_stream {
     PushLane lanes[2];
     int lane_next = 0;
     cudaStream_t tail_st = nullptr;  // ordering, formatting, statistics, result copies
+    cudaStream_t filt_st = nullptr;  // residual path: the filters
+    cudaEvent_t lmax_ev[kLmaxEv] = {};   // [push n % kLmaxEv]: its 3x3 pass done
     int2* d_yx = nullptr;
     int yx_cap = 0;
     int2* h_yx = nullptr;           // page-locked staging of the dynspec coordinates
@@ -164,7 +173,7 @@ struct lpf_stream {
     int n_strips = 0;
 
     bool profiling = false;
-    cudaEvent_t ev[kMaxSlots][ST_N + 1] = {};
+    cudaEvent_t ev[kMaxSlots][ST_N][2] = {};   // begin / end of every stage of a slot
     bool prof_slot[kMaxSlots] = {};
     double prof_ms[ST_N] = {};
     int64_t prof_n[ST_N] = {};
@@ -199,17 +208,17 @@ void free_all(lpf_stream* s) {
     cudaSetDevice(s->dev);
     if (s->st) cudaStreamSynchronize(s->st);
     if (s->tail_st) cudaStreamSynchronize(s->tail_st);
-    void* ptrs[] = {s->ring, s->resring, s->D, s->xkeys, s->xvals, s->stage, s->d_lag, s->d_chg, s->d_member_start, s->d_member_ord,
+    if (s->filt_st) cudaStreamSynchronize(s->filt_st);
+    void* ptrs[] = {s->ring, s->resring, s->D, s->D2, s->stage, s->d_lag, s->d_chg, s->d_member_start, s->d_member_ord,
                     s->d_ord2d, s->d_dmax, s->d_yx};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& L : s->lanes) {
-        void* lp[] = {L.keys[0], L.keys[1], L.vals[0], L.vals[1], L.counter, L.ord, L.partials};
+        void* lp[] = {L.keys[0], L.keys[1], L.vals[0], L.vals[1], L.counter, L.ord, L.partials, L.xkeys, L.xvals};
         for (void* p : lp)
             if (p) cudaFree(p);
-        if (L.filter_done) cudaEventDestroy(L.filter_done);
-        if (L.lmax_done) cudaEventDestroy(L.lmax_done);
-        if (L.tail_done) cudaEventDestroy(L.tail_done);
+        for (cudaEvent_t e : {L.dd_done, L.rw_done, L.filter_done, L.tail_done})
+            if (e) cudaEventDestroy(e);
     }
     for (int i = 0; i < kMaxSlots; ++i) {
         if (s->slots[i].d_out) cudaFree(s->slots[i].d_out);
@@ -217,8 +226,11 @@ void free_all(lpf_stream* s) {
         if (s->slots[i].done) cudaEventDestroy(s->slots[i].done);
     }
     for (auto& row : s->ev)
-        for (auto& e : row)
-            if (e) cudaEventDestroy(e);
+        for (auto& st : row)
+            for (auto& e : st)
+                if (e) cudaEventDestroy(e);
+    for (auto& e : s->lmax_ev)
+        if (e) cudaEventDestroy(e);
     if (s->h_count) cudaFreeHost(s->h_count);
     if (s->h_yx) cudaFreeHost(s->h_yx);
     if (s->yx_copied) cudaEventDestroy(s->yx_copied);
@@ -245,6 +257,7 @@ void free_all(lpf_stream* s) {
     }
     if (s->copy_st) cudaStreamDestroy(s->copy_st);
     if (s->tail_st) cudaStreamDestroy(s->tail_st);
+    if (s->filt_st) cudaStreamDestroy(s->filt_st);
     if (s->own_stream && s->st) cudaStreamDestroy(s->st);
 }
 
@@ -406,10 +419,10 @@ lpf::ResArgs res_args(lpf_stream* s, const lpf::FilterArgs& a, int Tmod, const P
     ra.ring = s->ring;
     ra.lag = s->d_lag;
     ra.F = s->F;
-    ra.depth = s->depth;
+    ra.depth = s->ring_n;
     ra.Tmod = Tmod;
-    ra.xkeys = s->xkeys;
-    ra.xvals = s->xvals;
+    ra.xkeys = L.xkeys;
+    ra.xvals = L.xvals;
     ra.xcounter = reinterpret_cast<unsigned long long*>(L.counter + 2);
     ra.xcap = s->xcap;
     ra.band_k = s->prm.mode == LPF_MODE_SUBBAND ? s->prm.lmax_r : 0;
@@ -417,13 +430,14 @@ lpf::ResArgs res_args(lpf_stream* s, const lpf::FilterArgs& a, int Tmod, const P
 }
 
 template <typename TS>
-void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows, int Tmod, const PushLane& L) {
+void launch_filter_res(lpf_stream* s, const lpf::FilterArgs& a, int n_rows, int Tmod, const PushLane& L,
+                       cudaStream_t st) {
     const lpf::ResArgs ra = res_args(s, a, Tmod, L);
     dim3 grid((unsigned)s->n_strips, (unsigned)n_rows, (unsigned)s->fseg);
     if (s->prm.box_r == 7)
-        lpf::k_filter_res<7, TS><<<grid, lpf::FiltGeom<7>::NT, lpf::res_filter_smem_bytes<7>(), s->st>>>(ra);
+        lpf::k_filter_res<7, TS><<<grid, lpf::FiltGeom<7>::NT, lpf::res_filter_smem_bytes<7>(), st>>>(ra);
     else
-        lpf::k_filter_res<15, TS><<<grid, lpf::FiltGeom<15>::NT, lpf::res_filter_smem_bytes<15>(), s->st>>>(ra);
+        lpf::k_filter_res<15, TS><<<grid, lpf::FiltGeom<15>::NT, lpf::res_filter_smem_bytes<15>(), st>>>(ra);
 }
 
 template <typename TS>
@@ -463,7 +477,7 @@ void launch_dedisperse_ring(lpf_stream* s, const void* ring_v, float* out, int n
     auto go = [&](auto kern, int px) {
         dim3 grid((unsigned)((s->P / px + 255) / 256), (unsigned)nseg);
         kern<<<grid, 256, smem, s->st>>>(reinterpret_cast<const TS*>(ring_v), out, s->d_lag, s->d_chg, F,
-                                         s->depth, Tmod, n_rows, seg, s->P);
+                                         s->ring_n, Tmod, n_rows, seg, s->P);
     };
     if constexpr (sizeof(TS) == 4) {
         if (F == 8) go(lpf::k_dedisperse<8, true>, 4);
@@ -486,11 +500,11 @@ void launch_dedisperse_ring(lpf_stream* s, const void* ring_v, float* out, int n
 // ring (D itself is summed from the raw ring only on the 3x3 windows of the
 // threshold crossings).
 template <typename TS>
-void launch_dedisperse(lpf_stream* s, int n_rows, int Tmod) {
+void launch_dedisperse(lpf_stream* s, float* out, int n_rows, int Tmod) {
     if (s->stream_filter) {
-        launch_dedisperse_ring<TS>(s, s->resring, s->D, n_rows, Tmod);
+        launch_dedisperse_ring<TS>(s, s->resring, out, n_rows, Tmod);
     } else {
-        launch_dedisperse_ring<TS>(s, s->ring, s->D, n_rows, Tmod);
+        launch_dedisperse_ring<TS>(s, s->ring, out, n_rows, Tmod);
     }
 }
 
@@ -500,7 +514,7 @@ void launch_dynspec(lpf_stream* s, int n, int Tw, int slot_first, float* out) {
     int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 32);
     if (blocks < 1) blocks = 1;
     lpf::k_dynspec<TS><<<blocks, 256, 0, s->st>>>(reinterpret_cast<const TS*>(s->ring), s->d_yx, n,
-                                                  s->F, Tw, s->depth, slot_first, s->P, s->H, s->W,
+                                                  s->F, Tw, s->ring_n, slot_first, s->P, s->H, s->W,
                                                   s->prm.dyn_box_r, out);
 }
 
@@ -516,8 +530,12 @@ size_t filter_smem_bytes(int r, int rmax) {
     return floats * sizeof(float);
 }
 
-void prof_mark(lpf_stream* s, int sl, int i, cudaStream_t st = nullptr) {
-    if (s->profiling) cudaEventRecord(s->ev[sl][i], st ? st : s->st);
+// begin / end of stage i of slot sl on the stream the stage runs on
+void prof_begin(lpf_stream* s, int sl, int i, cudaStream_t st) {
+    if (s->profiling) cudaEventRecord(s->ev[sl][i][0], st);
+}
+void prof_end(lpf_stream* s, int sl, int i, cudaStream_t st) {
+    if (s->profiling) cudaEventRecord(s->ev[sl][i][1], st);
 }
 
 // Accumulate the stage times of a finished slot (its done event has completed).
@@ -525,7 +543,7 @@ void prof_collect(lpf_stream* s, int sl) {
     if (!s->prof_slot[sl]) return;
     for (int i = 0; i < ST_N; ++i) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, s->ev[sl][i], s->ev[sl][i + 1]) == cudaSuccess) {
+        if (cudaEventElapsedTime(&ms, s->ev[sl][i][0], s->ev[sl][i][1]) == cudaSuccess) {
             s->prof_ms[i] += ms;
             s->prof_n[i] += 1;
         } else {
@@ -538,14 +556,25 @@ void prof_collect(lpf_stream* s, int sl) {
 int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
     const int sl = s->next_slot;
     Slot& slot = s->slots[sl];
-    const int64_t ring_slot = T % s->depth;
+    const int64_t ring_slot = T % s->ring_n;
     const int Tmod = (int)ring_slot;
     const int n_rows = n_active_rows(s, T);
     const int p = s->lane_next;
     PushLane& L = s->lanes[p];
+    const int64_t seq = s->frames_pushed;      // push sequence number
     cudaGetLastError();
 
-    prof_mark(s, sl, ST_INGEST);
+    const bool clip = s->clip;
+    // Residual path: the residuals and their shift-sum come from the pushed frame
+    // and the residual ring, so the raw ring write of this frame follows the
+    // shift-sum; the filter runs on its own stream, beside the next push's
+    // residuals and shift-sum, on this lane's image buffer and crossing list.
+    const bool late_ring = s->stream_filter && !clip;
+    cudaStream_t fs = late_ring ? s->filt_st : s->st;
+    cudaStream_t ts = s->tail_st;
+    float* images = (late_ring && p == 1) ? s->D2 : s->D;
+
+    prof_begin(s, sl, ST_INGEST, s->st);
     if (s->prm.qc) {
         lpf::k_qc_scan<<<dim3(lpf::kQcScanBlocks, s->F), 256, 0, s->st>>>(
             frame_dev, s->HW, s->qc_mean, s->qc_m2, s->qc_n, s->P, s->prm.qc_min_frames, s->prm.qc_zeta,
@@ -560,13 +589,6 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
             default: launch_ingest<__nv_bfloat16>(s, frame_dev, ring_slot); break;
         }
     };
-    const bool clip = s->clip;
-    // Residual path: the residuals and their shift-sum come from the pushed frame
-    // and the residual ring, so the raw ring write of this frame waits until after
-    // the shift-sum; by then the previous push's 3x3 pass (tail stream), which may
-    // read the frame this write replaces, has long finished.
-    const bool late_ring = s->stream_filter && !clip;
-    PushLane& Lprev = s->lanes[p ^ 1];
     if (late_ring) {
         switch (s->prm.dtype) {
             case LPF_FP32: launch_residual<float>(s, frame_dev, ring_slot); break;
@@ -576,13 +598,15 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
     } else {
         ingest();
     }
-    // this lane's buffers were last used by the push two back: its tail must be done
+    // this lane's buffers (images, crossing list, candidates) were last used by the
+    // push two back: its tail, which follows its filter, must be done
     LPF_TRY(cudaStreamWaitEvent(s->st, L.tail_done, 0));
     lpf::k_zero_u32<<<1, 32, 0, s->st>>>(L.counter, 4);   // candidates, crossings (u64 at word 2)
-    prof_mark(s, sl, ST_DEDISP);
+    prof_end(s, sl, ST_INGEST, s->st);
+    prof_begin(s, sl, ST_DEDISP, s->st);
     // images the filter reads: D - C per distinct delay row, or (per-subband
     // detector) the residual planes of the newest frame, in place for FP32
-    const float* filter_images = s->D;
+    const float* filter_images = images;
     lpf::ClipArgs ca{};
     if (clip) {
         // planes clipped: the F band images of the newest frame (per-subband
@@ -622,9 +646,9 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
                 }
             } else {
                 switch (s->prm.dtype) {
-                    case LPF_FP32: launch_dedisperse<float>(s, n_rows, Tmod); break;
-                    case LPF_FP16: launch_dedisperse<__half>(s, n_rows, Tmod); break;
-                    default: launch_dedisperse<__nv_bfloat16>(s, n_rows, Tmod); break;
+                    case LPF_FP32: launch_dedisperse<float>(s, s->D, n_rows, Tmod); break;
+                    case LPF_FP16: launch_dedisperse<__half>(s, s->D, n_rows, Tmod); break;
+                    default: launch_dedisperse<__nv_bfloat16>(s, s->D, n_rows, Tmod); break;
                 }
                 LPF_TRY(cudaMemsetAsync(s->clip_flags, 0, (size_t)np * s->P, s->st));
             }
@@ -650,25 +674,34 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
             filter_images = reinterpret_cast<const float*>(s->resring) + ring_slot * n;
         } else if (s->prm.dtype == LPF_FP16) {
             lpf::k_band_planes<__half><<<148 * 8, 256, 0, s->st>>>(
-                reinterpret_cast<const __half*>(s->resring) + ring_slot * n, s->D, n);
+                reinterpret_cast<const __half*>(s->resring) + ring_slot * n, images, n);
         } else {
             lpf::k_band_planes<__nv_bfloat16><<<148 * 8, 256, 0, s->st>>>(
-                reinterpret_cast<const __nv_bfloat16*>(s->resring) + ring_slot * n, s->D, n);
+                reinterpret_cast<const __nv_bfloat16*>(s->resring) + ring_slot * n, images, n);
         }
     } else if (n_rows > 0) {
         switch (s->prm.dtype) {
-            case LPF_FP32: launch_dedisperse<float>(s, n_rows, Tmod); break;
-            case LPF_FP16: launch_dedisperse<__half>(s, n_rows, Tmod); break;
-            default: launch_dedisperse<__nv_bfloat16>(s, n_rows, Tmod); break;
+            case LPF_FP32: launch_dedisperse<float>(s, images, n_rows, Tmod); break;
+            case LPF_FP16: launch_dedisperse<__half>(s, images, n_rows, Tmod); break;
+            default: launch_dedisperse<__nv_bfloat16>(s, images, n_rows, Tmod); break;
         }
     }
-    prof_mark(s, sl, ST_RINGW);
+    prof_end(s, sl, ST_DEDISP, s->st);
+    if (late_ring) LPF_TRY(cudaEventRecord(L.dd_done, s->st));
+    prof_begin(s, sl, ST_RINGW, s->st);
     if (late_ring) {
-        // the previous 3x3 pass also reads the crossing list the filter rewrites
-        LPF_TRY(cudaStreamWaitEvent(s->st, Lprev.lmax_done, 0));
+        // the raw ring write replaces the frame T - slots, which the 3x3 passes of
+        // the pushes up to T - slots + max_delay read: wait for the last of them (the
+        // tail stream runs them in order; an event re-recorded by a later push is a
+        // later pass, so waiting on it is safe)
+        const int64_t back = (int64_t)s->ring_n - s->max_delay;
+        if (seq >= back) LPF_TRY(cudaStreamWaitEvent(s->st, s->lmax_ev[(seq - back) % kLmaxEv], 0));
         ingest();
+        LPF_TRY(cudaEventRecord(L.rw_done, s->st));
     }
-    prof_mark(s, sl, ST_FILTER);
+    prof_end(s, sl, ST_RINGW, s->st);
+    if (late_ring) LPF_TRY(cudaStreamWaitEvent(fs, L.dd_done, 0));
+    prof_begin(s, sl, ST_FILTER, fs);
     lpf::FilterArgs a;
     if (n_rows > 0) {
         a.D = filter_images; a.P = s->P; a.H = s->H; a.W = s->W; a.r = s->prm.box_r; a.kappa = s->prm.kappa;
@@ -681,11 +714,12 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
                 ca, a, s->prm.lmax_r);
         } else if (s->stream_filter) {
             switch (s->prm.dtype) {
-                case LPF_FP32: launch_filter_res<float>(s, a, n_rows, Tmod, L); break;
-                case LPF_FP16: launch_filter_res<__half>(s, a, n_rows, Tmod, L); break;
-                default: launch_filter_res<__nv_bfloat16>(s, a, n_rows, Tmod, L); break;
+                case LPF_FP32: launch_filter_res<float>(s, a, n_rows, Tmod, L, fs); break;
+                case LPF_FP16: launch_filter_res<__half>(s, a, n_rows, Tmod, L, fs); break;
+                default: launch_filter_res<__nv_bfloat16>(s, a, n_rows, Tmod, L, fs); break;
             }
         } else {
+            a.D = s->D;
             dim3 grid((unsigned)(s->tiles_x * s->tiles_y), (unsigned)n_rows);
             if (s->filter_rmax == 8)
                 lpf::k_filter<8><<<grid, lpf::kFilterThreads, s->filter_smem, s->st>>>(a);
@@ -693,14 +727,14 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
                 lpf::k_filter<16><<<grid, lpf::kFilterThreads, s->filter_smem, s->st>>>(a);
         }
     }
+    prof_end(s, sl, ST_FILTER, fs);
     // the tail of this push (3x3 pass, ordering, formatting, statistics, copies)
-    // on the tail stream once its filter is done, after the tail of the previous
-    // push (same stream, other lane); the main stream moves on to the next push's
-    // residuals and shift-sum
-    LPF_TRY(cudaEventRecord(L.filter_done, s->st));
-    cudaStream_t ts = s->tail_st;
+    // on the tail stream once its filter (and raw ring write) is done, after the
+    // tail of the previous push (same stream, other lane)
+    LPF_TRY(cudaEventRecord(L.filter_done, fs));
     LPF_TRY(cudaStreamWaitEvent(ts, L.filter_done, 0));
-    prof_mark(s, sl, ST_LMAX, ts);
+    if (late_ring) LPF_TRY(cudaStreamWaitEvent(ts, L.rw_done, 0));
+    prof_begin(s, sl, ST_LMAX, ts);
     if (n_rows > 0 && late_ring) {
         switch (s->prm.dtype) {
             case LPF_FP32: launch_lmax_res<float>(s, a, Tmod, L, ts); break;
@@ -708,8 +742,8 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
             default: launch_lmax_res<__nv_bfloat16>(s, a, Tmod, L, ts); break;
         }
     }
-    LPF_TRY(cudaEventRecord(L.lmax_done, ts));
-    prof_mark(s, sl, ST_SORT, ts);
+    prof_end(s, sl, ST_LMAX, ts);
+    LPF_TRY(cudaEventRecord(s->lmax_ev[seq % kLmaxEv], ts));
     // ordering: counting sort on the trial rank, then each rank's bucket sorted by
     // pixel and formatted (lpf_order.cuh)
     {
@@ -717,20 +751,23 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
         unsigned* counts = L.ord;
         unsigned* start = L.ord + n_ord;
         unsigned* cursor = L.ord + 2 * n_ord;
+        prof_begin(s, sl, ST_SORT, ts);
         lpf::k_ord_count<<<kSortBlocks, lpf::kOrdThreads, 0, ts>>>(L.keys[0], L.counter, s->prm.cand_cap, shift,
                                                                    n_ord, counts);
         lpf::k_ord_scan<<<1, 1024, 0, ts>>>(counts, n_ord, start, cursor);
         lpf::k_ord_scatter<<<kSortBlocks, lpf::kOrdThreads, 0, ts>>>(L.keys[0], L.vals[0], L.counter,
                                                                      s->prm.cand_cap, shift, cursor, L.keys[1],
                                                                      L.vals[1]);
-        prof_mark(s, sl, ST_FORMAT, ts);
+        prof_end(s, sl, ST_SORT, ts);
+        prof_begin(s, sl, ST_FORMAT, ts);
         lpf::k_ord_sort_format<<<std::min(n_ord, 148 * 8), lpf::kOrdThreads, lpf::ord_sort_smem_bytes(), ts>>>(
             L.keys[1], L.vals[1], start, cursor, n_ord, slot.d_out, s->d_ord2d, s->d_dmax, T, s->bx, s->by);
+        prof_end(s, sl, ST_FORMAT, ts);
     }
-    prof_mark(s, sl, ST_STATS, ts);
+    prof_begin(s, sl, ST_STATS, ts);
     if (n_rows > 0)
         lpf::k_stats<<<n_rows, 256, 0, ts>>>(L.partials, n_filter_blocks(s), slot.d_stats);
-    prof_mark(s, sl, ST_N, ts);
+    prof_end(s, sl, ST_STATS, ts);
     if (cudaGetLastError() != cudaSuccess) return LPF_E_CUDA;
     LPF_TRY(cudaMemcpyAsync(s->h_count + sl, L.counter, sizeof(unsigned), cudaMemcpyDeviceToHost, ts));
     if (s->prm.qc)
@@ -886,6 +923,10 @@ int plan_stream(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, 
     s->clip_planes_n = band ? F : s->n_distinct;
     s->stream_filter = !s->clip && (band || prm.filter_impl == 2 ||
                                     (prm.filter_impl == 0 && (prm.box_r == 7 || prm.box_r == 15)));
+    // the residual path writes the raw ring after the shift-sum, while 3x3 passes of
+    // earlier pushes may still read it: two spare slots keep that write from
+    // waiting on the pass just before it
+    s->ring_n = buffer_depth + ((s->stream_filter && !s->clip) ? kSpareSlots : 0);
     s->n_strips = (W + lpf::kStreamTX - 1) / lpf::kStreamTX;
     // the per-subband detector has only F rows: split each strip into row segments
     // so that about two waves of 4 CTAs per SM run (each segment after the first
@@ -911,9 +952,10 @@ int plan_stream(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, 
 size_t footprint_bytes(const lpf_stream* s) {
     auto b = [](size_t n) { return std::max<size_t>(n, 16); };
     const size_t nd = (size_t)s->n_distinct, cap = (size_t)s->prm.cand_cap;
-    size_t t = (size_t)s->depth * s->F * s->P * s->elem * (s->stream_filter ? 2 : 1);
-    t += b(nd * s->P * 4) + b(2 * (size_t)s->F * s->HW * 4) + b(nd * s->F * 2) + b(nd * 4);
-    if (s->xcap > 0) t += b((size_t)s->xcap * 8) + b((size_t)s->xcap * 4);
+    const bool two = s->stream_filter && !s->clip;   // filter beside the next push: two image buffers
+    size_t t = (size_t)s->ring_n * s->F * s->P * s->elem * (s->stream_filter ? 2 : 1);
+    t += b(nd * s->P * 4) * (two ? 2 : 1) + b(2 * (size_t)s->F * s->HW * 4) + b(nd * s->F * 2) + b(nd * 4);
+    if (s->xcap > 0) t += 2 * (b((size_t)s->xcap * 8) + b((size_t)s->xcap * 4));
     if (s->clip)
         t += b((size_t)s->clip_planes_n * s->P) + b(5 * (size_t)s->clip_planes_n * s->P * 4) +
              b((size_t)s->prm.clip_iters * 4) +
@@ -972,6 +1014,9 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
     // default priority: a higher one lets the tail's blocks take SMs ahead of the
     // next push's residuals and shift-sum, which then finish later (measured)
     if (rc == LPF_OK && cudaStreamCreateWithFlags(&s->tail_st, cudaStreamNonBlocking) != cudaSuccess) rc = LPF_E_CUDA;
+    if (rc == LPF_OK && cudaStreamCreateWithFlags(&s->filt_st, cudaStreamNonBlocking) != cudaSuccess) rc = LPF_E_CUDA;
+    for (int i = 0; i < kLmaxEv && rc == LPF_OK; ++i)
+        if (cudaEventCreateWithFlags(&s->lmax_ev[i], cudaEventDisableTiming) != cudaSuccess) rc = LPF_E_CUDA;
     for (int i = 0; i < 2 && rc == LPF_OK; ++i)
         if (cudaEventCreateWithFlags(&s->stage_ready[i], cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&s->stage_free[i], cudaEventDisableTiming) != cudaSuccess)
@@ -983,7 +1028,7 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
     if (rc == LPF_OK) rc = set_res_attributes<float>();
     if (rc == LPF_OK) rc = set_res_attributes<__half>();
     if (rc == LPF_OK) rc = set_res_attributes<__nv_bfloat16>();
-    const size_t ring_elems = (size_t)buffer_depth * F * s->P;
+    const size_t ring_elems = (size_t)s->ring_n * F * s->P;
     if (rc == LPF_OK) {
         if (cudaMalloc(&s->ring, ring_elems * s->elem) != cudaSuccess) { cudaGetLastError(); rc = LPF_E_OOM; }
         else s->device_bytes += ring_elems * s->elem;
@@ -995,9 +1040,8 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
         if (rc == LPF_OK && cudaMemsetAsync(s->resring, 0, ring_elems * s->elem, s->st) != cudaSuccess) rc = LPF_E_CUDA;
     }
     if (rc == LPF_OK) rc = dev_alloc(s, &s->D, (size_t)s->n_distinct * s->P);
+    if (rc == LPF_OK && s->stream_filter && !s->clip) rc = dev_alloc(s, &s->D2, (size_t)s->n_distinct * s->P);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->stage, 2 * (size_t)F * s->HW);
-    if (rc == LPF_OK && s->xcap > 0) rc = dev_alloc(s, &s->xkeys, (size_t)s->xcap);
-    if (rc == LPF_OK && s->xcap > 0) rc = dev_alloc(s, &s->xvals, (size_t)s->xcap);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_lag, (size_t)s->n_distinct * F);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_chg, (size_t)s->n_distinct);
     if (rc == LPF_OK) rc = dev_alloc(s, &s->d_member_start, s->member_start.size());
@@ -1010,12 +1054,15 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
             if (rc == LPF_OK) rc = dev_alloc(s, &L.vals[i], (size_t)prm.cand_cap);
         }
         if (rc == LPF_OK) rc = dev_alloc(s, &L.counter, 4);
+        if (rc == LPF_OK && s->xcap > 0) rc = dev_alloc(s, &L.xkeys, (size_t)s->xcap);
+        if (rc == LPF_OK && s->xcap > 0) rc = dev_alloc(s, &L.xvals, (size_t)s->xcap);
         if (rc == LPF_OK) rc = dev_alloc(s, &L.ord, (size_t)3 * s->n_dm);
         // the rank counts start at zero; the scan clears them after every push
         if (rc == LPF_OK && cudaMemsetAsync(L.ord, 0, (size_t)3 * s->n_dm * 4, s->st) != cudaSuccess) rc = LPF_E_CUDA;
         if (rc == LPF_OK) rc = dev_alloc(s, &L.partials, (size_t)s->n_distinct * n_filter_blocks(s) * 3);
         if (rc == LPF_OK && (cudaEventCreateWithFlags(&L.filter_done, cudaEventDisableTiming) != cudaSuccess ||
-                             cudaEventCreateWithFlags(&L.lmax_done, cudaEventDisableTiming) != cudaSuccess ||
+                             cudaEventCreateWithFlags(&L.dd_done, cudaEventDisableTiming) != cudaSuccess ||
+                             cudaEventCreateWithFlags(&L.rw_done, cudaEventDisableTiming) != cudaSuccess ||
                              cudaEventCreateWithFlags(&L.tail_done, cudaEventDisableTiming) != cudaSuccess))
             rc = LPF_E_CUDA;
     }
@@ -1058,8 +1105,9 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
         }
     }
     for (int k = 0; k < s->n_slots && rc == LPF_OK; ++k)
-        for (int i = 0; i <= ST_N && rc == LPF_OK; ++i)
-            if (cudaEventCreate(&s->ev[k][i]) != cudaSuccess) rc = LPF_E_CUDA;
+        for (int i = 0; i < ST_N && rc == LPF_OK; ++i)
+            for (int e = 0; e < 2 && rc == LPF_OK; ++e)
+                if (cudaEventCreate(&s->ev[k][i][e]) != cudaSuccess) rc = LPF_E_CUDA;
     if (rc == LPF_OK) {
         if (cudaMallocHost(&s->h_count, sizeof(unsigned) * kMaxSlots) != cudaSuccess ||
             cudaMallocHost(&s->h_stats, sizeof(double) * kMaxSlots * s->n_distinct * 3) != cudaSuccess) {
@@ -1220,7 +1268,7 @@ int lpf_extract_dynspec(lpf_stream* s, const lpf_candidate* c_host, int n, int T
     }
     LPF_TRY(cudaMemcpyAsync(s->d_yx, s->h_yx, (size_t)n * sizeof(int2), cudaMemcpyHostToDevice, s->st));
     LPF_TRY(cudaEventRecord(s->yx_copied, s->st));
-    int slot_first = (int)((T - Tw + 1) % s->depth);
+    int slot_first = (int)((T - Tw + 1) % s->ring_n);
     cudaGetLastError();
     switch (s->prm.dtype) {
         case LPF_FP32: launch_dynspec<float>(s, n, Tw, slot_first, out_dev); break;
@@ -1257,7 +1305,7 @@ int lpf_stream_info(const lpf_stream* s, lpf_stream_info_t* out) {
     if (!s || !out) return LPF_E_ARG;
     out->H = s->H; out->W = s->W; out->F = s->F; out->n_dm = s->n_dm; out->depth = s->depth;
     out->dtype = s->prm.dtype; out->n_distinct = s->n_distinct; out->max_delay = s->max_delay;
-    out->ring_bytes = (size_t)s->depth * s->F * s->P * s->elem;
+    out->ring_bytes = (size_t)s->ring_n * s->F * s->P * s->elem;
     out->device_bytes = s->device_bytes;
     out->frames_pushed = s->frames_pushed;
     out->last_T = s->last_T;
@@ -1268,6 +1316,7 @@ int lpf_stream_sync(lpf_stream* s) {
     if (!s) return LPF_E_ARG;
     if (cudaSetDevice(s->dev) != cudaSuccess) return LPF_E_CUDA;
     int rc = cuda_fail(cudaStreamSynchronize(s->st));
+    if (rc == LPF_OK && s->filt_st) rc = cuda_fail(cudaStreamSynchronize(s->filt_st));
     if (rc == LPF_OK && s->tail_st) rc = cuda_fail(cudaStreamSynchronize(s->tail_st));
     return rc;
 }
@@ -1374,7 +1423,7 @@ void launch_dynspec_records(lpf_stream* s, const lpf::CandidateRec* rec, int n, 
     int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 32);
     if (blocks < 1) blocks = 1;
     k_dynspec_records<TS><<<blocks, 256, 0, s->st>>>(reinterpret_cast<const TS*>(s->ring), rec, n, s->F, Tw,
-                                                     s->depth, slot_first, s->P, s->H, s->W,
+                                                     s->ring_n, slot_first, s->P, s->H, s->W,
                                                      s->prm.dyn_box_r, out);
 }
 
@@ -1399,7 +1448,7 @@ extern "C" int lpf_extract_dynspec_static(lpf_stream* s, const lpf_candidate* c_
     if (rc != LPF_OK) return rc;
     // every call writes the records it reads: nothing carries over between calls
     LPF_TRY(cudaMemcpyAsync(rec, c_host, (size_t)n * sizeof(lpf_candidate), cudaMemcpyHostToDevice, s->st));
-    const int slot_first = (int)((T - Tw + 1) % s->depth);
+    const int slot_first = (int)((T - Tw + 1) % s->ring_n);
     cudaGetLastError();
     switch (s->prm.dtype) {
         case LPF_FP32: launch_dynspec_records<float>(s, rec, n, Tw, slot_first, out_dev); break;

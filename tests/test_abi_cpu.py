@@ -99,19 +99,24 @@ def test_footprint_is_planned_without_a_gpu():
     sp = synth.spec_aartfaac()
     fp32 = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth)
     fp16 = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth, dtype="fp16")
-    ring32 = sp.depth * sp.F * sp.H * sp.W * 4
-    # raw + residual rings (box 31 uses the residual path), 205 images of D - C,
-    # two staging frames, candidate buffers
-    imgs = 205 * sp.H * sp.W * 4
-    assert 2 * ring32 + imgs < fp32 < 2 * ring32 + imgs + 400 * 2 ** 20
-    assert fp32 - fp16 == ring32
+    plane = sp.F * sp.H * sp.W * 4                 # one FP32 frame
+    # residual path (box 31): raw and residual rings of depth + 2 slots (the raw-ring
+    # write follows the shift-sum), two sets of the 205 images of D - C and two
+    # crossing lists (12 bytes for 1/32 of all pixels of the 205 delay rows; the
+    # filter of a push runs beside the next push's shift-sum), staging frames and
+    # candidate buffers
+    rings = 2 * (sp.depth + 2) * plane
+    imgs = 2 * 205 * sp.H * sp.W * 4
+    xlists = 2 * 12 * (205 * sp.H * sp.W // 32)
+    assert rings + imgs + xlists < fp32 < rings + imgs + xlists + 400 * 2 ** 20
+    assert fp32 - fp16 == (sp.depth + 2) * plane
     deeper = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth + 10)
-    assert deeper - fp32 == 2 * 10 * sp.F * sp.H * sp.W * 4
+    assert deeper - fp32 == 2 * 10 * plane
     tiled = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth, filter_impl="tiled")
-    # the residual ring and the crossing list (12 bytes for 1/32 of all pixels of
-    # the 205 delay rows); partials: strips vs tiles
-    xlist = 12 * (205 * sp.H * sp.W // 32)
-    assert abs(fp32 - tiled - ring32 - xlist) < 4 * 2 ** 20
+    # the tiled path: the raw ring of depth slots and one set of images, no residual
+    # ring or crossing list; partials: strips vs tiles
+    extra = (sp.depth + 2) * plane + 2 * plane + 205 * sp.H * sp.W * 4 + xlists
+    assert abs(fp32 - tiled - extra) < 4 * 2 ** 20
     with pytest.raises(lpf.LpfError) as e:
         lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, 40)
     assert e.value.code == lpf.LPF_E_DEPTH
@@ -125,7 +130,9 @@ def test_stress_config_depth_96_is_rejected():
         lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth, dtype="fp16")
     assert e.value.code == lpf.LPF_E_DEPTH
     fp = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, 114, dtype="fp16")
-    assert 72e9 < fp < 80e9        # 2 x 30.6 GB rings (raw, residual) + 13.8 GB images of D - C
+    # 2 x 31.1 GB rings (raw, residual; 116 slots) + 2 x 14.2 GB images of D - C
+    # + 2 x 1.3 GB crossing lists
+    assert 90e9 < fp < 96e9
 
 
 def test_quality_control_footprint():
@@ -145,16 +152,18 @@ def test_subband_detector_footprint():
     import synth
     sp = synth.spec_aartfaac(H=256, W=256)
     fp = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, None, 2, mode="subband", lmax_r=3)
-    rings = 2 * 2 * sp.F * sp.H * sp.W * 4          # raw and residual rings, depth 2
-    imgs = sp.F * sp.H * sp.W * 4
+    rings = 2 * (2 + 2) * sp.F * sp.H * sp.W * 4    # raw and residual rings, depth 2 + 2 spare slots
+    imgs = 2 * sp.F * sp.H * sp.W * 4               # band planes, one set per lane
     # plus the 1M-record candidate, crossing and result buffers and two staging frames
-    assert rings + imgs < fp < rings + imgs + 128 * 2 ** 20
+    assert rings + imgs < fp < rings + imgs + 160 * 2 ** 20
 
 
 def test_clipping_footprint():
     """The clipping path (iterations, or the Gaussian kernel) adds a flag plane and
-    five FP32 planes per band and drops the residual ring (depth 2, FP32) and the
-    crossing list (max(cand_cap, F H W / 32) keys and S/N values)."""
+    five FP32 planes per band and drops what the box path needs beside them: the
+    residual ring (depth 2 + 2 spare slots, FP32), the two spare raw-ring slots,
+    the second set of band planes and the two crossing lists (max(cand_cap,
+    F H W / 32) keys and S/N values each)."""
     import synth
     sp = synth.spec_aartfaac(H=256, W=256)
     one = lpf.footprint(sp.H, sp.W, sp.freqs_mhz, None, 2, mode="subband", lmax_r=3)
@@ -163,7 +172,7 @@ def test_clipping_footprint():
                           gauss_sigma=4.0, box_r=9)
     px = sp.F * sp.H * sp.W
     xcap = max(1 << 20, px // 32)
-    delta = px * 21 - 2 * px * 4 - xcap * 12
+    delta = px * 21 - (2 + 4) * px * 4 - px * 4 - 2 * xcap * 12
     # (+ the kernel factors and the statistics partials of the other block layout)
     assert delta <= many - one < delta + 65536
     assert delta <= gauss - one < delta + 65536
