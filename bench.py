@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-RESULT_SLOTS = 4                # result slots: up to 3 frames ahead of the oldest unpolled one
+RESULT_SLOTS = 8                # result slots: up to 7 frames ahead of the oldest unpolled one
 METRIC = "pixel*DM-trials/s"
 WORKLOAD = "aartfaac-1024x1024-16sb-251dm-depth48-box31"
 DTYPE_NAME = {"fp32": "f32", "fp16": "f16", "bf16": "bf16"}
