@@ -558,9 +558,36 @@ def run_ours(args):
                         "clocks": clocks.summary(f16["t_wall0"], f16["t_wall1"])}
     if serving is not None:
         line["serving"] = serving
+    if ws == 1:
+        line["cnn"] = cnn_throughput(lpf, torch)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec, delays)
     print(json.dumps(line), flush=True)
+
+
+def cnn_throughput(lpf, torch, n=10000, F=32, Tw=64, steps=20, warmup=3):
+    """The parameter-inference network on n F x Tw spectra already on the device
+    (synthetic noise, fixed random weights): spectra per second, CUDA-event timed
+    on the network's stream."""
+    st = torch.cuda.Stream()
+    x = torch.randn((n, F, Tw), device="cuda", dtype=torch.float32)
+    out = torch.empty((n, 5), device="cuda", dtype=torch.float32)
+    with lpf.Cnn(F, Tw, synth.cnn_params(3), max_batch=n, cuda_stream=st) as net:
+        torch.cuda.synchronize()
+        for _ in range(warmup):
+            net.forward(x, out=out, sync=False)
+        net.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            net.forward(x, out=out, sync=False)
+        e1.record(st)
+        net.sync()
+        ms = e0.elapsed_time(e1) / steps
+    flops = n * 2 * (F * Tw * 9 * 16 + (F // 2) * (Tw // 2) * 144 * 32 + (F // 4) * (Tw // 4) * 288 * 64)
+    return {"workload": f"{n} dynamic spectra of {F} x {Tw} (conv 1->16, 16->32, 32->64, head 64->5)",
+            "ms_per_batch": ms, "spectra_per_s": n / (ms / 1e3), "tflops": flops / (ms / 1e3) / 1e12,
+            "flop_per_batch": flops}
 
 
 def launches_per_push(spec, qc):
@@ -707,8 +734,9 @@ def run_subband(args):
 def run_stress(args):
     """Stress workload: 2048^2 px, 32 subbands (57.6-63.85 MHz), 1001 DM trials, FP16
     ring of depth 114 (the DM 500 sweep spans 113 frames).  Each step pushes a frame,
-    polls the oldest unpolled one and gathers the 32 x 64 FP32 dynamic spectra of its
-    candidates; frames per second against the 1 s cadence is the real-time factor.
+    polls the oldest unpolled one, gathers the 32 x 64 FP32 dynamic spectra of its
+    candidates and runs the parameter-inference network on them; frames per second
+    against the 1 s cadence is the real-time factor.
     The candidate load of about 1e4 per frame comes from 10 bright steady sources
     (each a candidate at every one of the 1001 trials): the 200 pulses give about 2."""
     import torch
@@ -724,6 +752,8 @@ def run_stress(args):
     Tw, T = 64, 0
     ncand, nds, gev = [], [], []
     gbuf = torch.empty((16384, spec.F, Tw), dtype=torch.float32, device="cuda")   # reused output batch
+    cnn_out = torch.empty((16384, 5), dtype=torch.float32, device="cuda")
+    net = lpf.Cnn(spec.F, Tw, synth.cnn_params(3), max_batch=16384, cuda_stream=cur)
 
     def poll_and_gather():
         Tp, c, n, _ = s.poll(timeout_ms=600000)
@@ -733,6 +763,7 @@ def run_stress(args):
             e[0].record(cur)
             c = c[: gbuf.shape[0]]
             s.dynspec(c, Tw, out=gbuf[: len(c)], sync=False)   # [n, 32, 64] FP32 on the search stream
+            net.forward(gbuf[: len(c)], out=cnn_out[: len(c)], sync=False)   # mu, L of every candidate
             e[1].record(cur)
             gev.append(e)
             g = len(c)
@@ -765,7 +796,8 @@ def run_stress(args):
     kt = s.kernel_times(reset=True)
     s.close()
     per_push = {n: kt[n][0] / max(kt[n][1], 1) for n in kt}
-    per_push["dynspec_gather"] = float(np.mean([a.elapsed_time(b) for a, b in gev])) if gev else 0.0
+    per_push["dynspec_gather_and_cnn"] = float(np.mean([a.elapsed_time(b) for a, b in gev])) if gev else 0.0
+    net.close()
     fps = args.steps / elapsed
     print(json.dumps({
         "metric": METRIC, "value": spec.H * spec.W * spec.n_dm * fps, "unit": METRIC,

@@ -353,6 +353,48 @@ int lpf_server_stats(lpf_server* srv, int id, lpf_serve_stats_t* out);
 /* Stop the worker, wait for all device work and release every stream. */
 int lpf_server_close(lpf_server* srv);
 
+/* ------------------------------------------------------------------------
+ * Parameter inference on the dynamic-spectrum batch (Sec. 2.3).
+ *
+ * The paper's network maps a candidate's dynamic spectrum to the mean mu and
+ * a Cholesky factor L (lower triangular, positive diagonal) of a Gaussian over
+ * its parameters theta, through convolutions with Leaky ReLU hidden states and
+ * a final linear layer; it gives the form, not the layers or the weights.
+ * This network, with weights the caller supplies, is:
+ *   conv1 3x3, 1 -> 16 channels, Leaky ReLU, 2x2 mean;
+ *   conv2 3x3, 16 -> 32, Leaky ReLU, 2x2 mean;
+ *   conv3 3x3, 32 -> 64, Leaky ReLU, mean over all pixels;
+ *   head: linear 64 -> 5, out = (mu0, mu1, exp z2 = L00, z3 = L10, exp z4 = L11);
+ * zero padding 1, alpha = 0.01.  conv2 and conv3 run on the tensor cores
+ * (BF16 weights and activations, FP32 sums); conv1 and the head in FP32.
+ *
+ * params: float32, lpf_cnn_param_count() values in this order: conv1.w
+ * [16][1][3][3], conv1.b [16], conv2.w [32][16][3][3], conv2.b [32], conv3.w
+ * [64][32][3][3], conv3.b [64], head.w [5][64], head.b [5] (HOST, copied).
+ */
+typedef struct lpf_cnn lpf_cnn;
+#define LPF_CNN_OUT 5
+
+size_t lpf_cnn_param_count(void);
+
+/* A network for F x Tw spectra (F subbands by Tw frames, as lpf_extract_dynspec
+ * writes them) and batches of at most max_batch; its work is enqueued on
+ * cuda_stream (NULL: a stream of its own) on the current device.  F and Tw
+ * multiples of 4, (F / 4) (Tw / 4) a power of two <= 128.  Errors: LPF_E_ARG,
+ * LPF_E_OOM, LPF_E_CUDA. */
+int lpf_cnn_open(lpf_cnn** out, int F, int Tw, const float* params, size_t n_params, int max_batch,
+                 void* cuda_stream);
+
+/* out_dev [n][5] (FP32, DEVICE) for the spectra x_dev [n][F][Tw] (FP32, DEVICE),
+ * n <= max_batch; asynchronous on the network's stream.  Errors: LPF_E_ARG,
+ * LPF_E_CUDA. */
+int lpf_cnn_forward(lpf_cnn* net, const float* x_dev, int n, float* out_dev);
+
+/* Wait for the network's work; LPF_E_TIMEOUT if a tensor-core completion wait
+ * ran out (its outputs are then not written). */
+int lpf_cnn_sync(lpf_cnn* net);
+int lpf_cnn_close(lpf_cnn* net);
+
 #ifdef __cplusplus
 }
 #endif

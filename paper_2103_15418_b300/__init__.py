@@ -33,7 +33,8 @@ EXPORTS = [
     "lpf_set_profiling", "lpf_get_kernel_times", "lpf_extract_dynspec_static",
     "lpf_stream_footprint", "lpf_server_open", "lpf_server_open_stream", "lpf_server_submit",
     "lpf_server_fetch", "lpf_server_close_stream", "lpf_server_stream_state", "lpf_server_stats",
-    "lpf_server_close",
+    "lpf_server_close", "lpf_cnn_param_count", "lpf_cnn_open", "lpf_cnn_forward", "lpf_cnn_sync",
+    "lpf_cnn_close",
 ]
 SERVE_PENDING, SERVE_ACTIVE, SERVE_CLOSED = 0, 1, 3
 MODES = {"dispersed": 0, "subband": 1}
@@ -132,6 +133,12 @@ def load(path: Optional[str] = None):
     lib.lpf_server_stream_state.argtypes = [c_void_p, c_int, POINTER(c_int)]
     lib.lpf_server_stats.argtypes = [c_void_p, c_int, POINTER(ServeStats)]
     lib.lpf_server_close.argtypes = [c_void_p]
+    lib.lpf_cnn_param_count.argtypes = []
+    lib.lpf_cnn_param_count.restype = c_size_t
+    lib.lpf_cnn_open.argtypes = [POINTER(c_void_p), c_int, c_int, c_void_p, c_size_t, c_int, c_void_p]
+    lib.lpf_cnn_forward.argtypes = [c_void_p, c_void_p, c_int, c_void_p]
+    lib.lpf_cnn_sync.argtypes = [c_void_p]
+    lib.lpf_cnn_close.argtypes = [c_void_p]
     _lib = lib
     return lib
 
@@ -406,6 +413,60 @@ class Server:
     def close(self) -> None:
         if getattr(self, "_h", None):
             load().lpf_server_close(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Cnn:
+    """The parameter-inference network on F x Tw dynamic spectra (Sec. 2.3), with
+    the caller's weights (float32 vector of lpf_cnn_param_count() values)."""
+
+    def __init__(self, F: int, Tw: int, params, max_batch: int, cuda_stream=None):
+        lib = load()
+        p = np.ascontiguousarray(params, dtype=np.float32).ravel()
+        if p.size != lib.lpf_cnn_param_count():
+            raise ValueError(f"{p.size} parameters, the network takes {lib.lpf_cnn_param_count()}")
+        h = c_void_p()
+        st = int(getattr(cuda_stream, "cuda_stream", cuda_stream)) if cuda_stream is not None else None
+        _check(lib.lpf_cnn_open(ctypes.byref(h), int(F), int(Tw), c_void_p(p.ctypes.data), p.size, int(max_batch),
+                                c_void_p(st) if st else None), "lpf_cnn_open")
+        self._h, self.F, self.Tw, self.max_batch = h, int(F), int(Tw), int(max_batch)
+
+    def forward(self, x, out=None, sync: bool = True):
+        """x: CUDA float32 [n, F, Tw] (contiguous) -> CUDA float32 [n, 5] =
+        (mu0, mu1, L00, L10, L11)."""
+        import torch
+        if not (x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+            raise ValueError("x must be a contiguous float32 CUDA tensor")
+        n = int(x.shape[0])
+        if tuple(x.shape) != (n, self.F, self.Tw):
+            raise ValueError(f"x shape {tuple(x.shape)} != (n, {self.F}, {self.Tw})")
+        if out is None:
+            out = torch.empty((n, 5), dtype=torch.float32, device=x.device)
+        optr = _out_ptr(out, (n, 5)) if n else 0
+        _check(load().lpf_cnn_forward(self._h, c_void_p(x.data_ptr()) if n else None, n,
+                                      c_void_p(optr) if n else None), "lpf_cnn_forward")
+        if sync:
+            self.sync()
+        return out
+
+    def sync(self) -> None:
+        _check(load().lpf_cnn_sync(self._h), "lpf_cnn_sync")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().lpf_cnn_close(self._h)
             self._h = None
 
     def __enter__(self):

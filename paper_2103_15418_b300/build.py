@@ -6,9 +6,9 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblpf.so")
-SOURCES = ["lpf_stream.cu", "lpf_server.cpp"]
+SOURCES = ["lpf_stream.cu", "lpf_server.cpp", "lpf_cnn.cu"]
 HEADERS = ["lpf_kernels.cuh", "lpf_dedisperse.cuh", "lpf_residual.cuh", "lpf_filter_res.cuh",
-           "lpf_filter_stream.cuh", "lpf_qc.cuh", "lpf_clip.cuh", "lpf_order.cuh", os.path.join("..", "..", "include", "lpf.h")]
+           "lpf_filter_stream.cuh", "lpf_qc.cuh", "lpf_clip.cuh", "lpf_order.cuh", "lpf_cnn.cuh", "lpf_tc.cuh", os.path.join("..", "..", "include", "lpf.h")]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",

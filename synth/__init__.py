@@ -241,3 +241,19 @@ def spec_stress(depth: int = 114, **kw) -> StreamSpec:
              rfi_fraction=0.01, rfi_amp=10.0, dtype="fp16")
     d.update(kw)
     return StreamSpec(**d)
+
+
+def cnn_params(seed: int = 3) -> np.ndarray:
+    """Fixed random weights of the parameter-inference network, float32, in the
+    order conv1.w [16][1][3][3], conv1.b [16], conv2.w [32][16][3][3], conv2.b [32],
+    conv3.w [64][32][3][3], conv3.b [64], head.w [5][64], head.b [5]: normal
+    draws scaled by sqrt(2 / fan_in) for the convolutions, 1/8 for the head, and
+    0.1 for the biases (seeded)."""
+    rng = np.random.Generator(np.random.Philox(key=[int(seed), 0xC44]))
+    parts = []
+    for shape, scale in [((16, 1, 3, 3), np.sqrt(2.0 / 9)), ((16,), 0.1),
+                         ((32, 16, 3, 3), np.sqrt(2.0 / 144)), ((32,), 0.1),
+                         ((64, 32, 3, 3), np.sqrt(2.0 / 288)), ((64,), 0.1),
+                         ((5, 64), 0.125), ((5,), 0.1)]:
+        parts.append((rng.standard_normal(shape) * scale).astype(np.float32).ravel())
+    return np.concatenate(parts)

@@ -225,3 +225,17 @@ def test_binding_refuses_buffers_the_library_would_overrun():
                 FakeCuda((5, 16, 12), contiguous=False), torch.zeros((5, 16, 12))):
         with pytest.raises(ValueError):
             lpf._out_ptr(bad, (5, 16, 12))
+
+
+def test_cnn_arguments_are_checked_before_any_cuda_call():
+    """F and Tw multiples of 4 with (F/4)(Tw/4) a power of two <= 128, the parameter
+    count and the batch limit are refused with LPF_E_ARG on a machine without a GPU."""
+    import synth
+    p = synth.cnn_params(1)
+    assert lpf.load().lpf_cnn_param_count() == p.size == 23621
+    for F, Tw, mb in [(12, 64, 4), (32, 66, 4), (8, 16, 0), (64, 64, 4), (2, 16, 4)]:
+        with pytest.raises(lpf.LpfError) as e:
+            lpf.Cnn(F, Tw, p, max_batch=mb)
+        assert e.value.code == lpf.LPF_E_ARG, (F, Tw, mb)
+    with pytest.raises(ValueError):
+        lpf.Cnn(8, 16, p[:-1], max_batch=4)
