@@ -80,10 +80,12 @@ __device__ __forceinline__ void hsum_sq_run(const float* __restrict__ in, int c0
 //      columns, lane = row                                               -> hE
 //   3. warps 0-3, one column each: vertical window sum as the suffix of the
 //      previous (2r+1)-row segment plus the prefix of the current one (exact)
-//      -> S(ys), ys = row - r; snr = R(ys)/sqrt(S), stats; the snr is parked in
-//      block k's R buffer and candidates are resolved once per block.  R(ys)
-//      of the first r rows lies in block k-1, whose buffer is being refilled:
-//      it is read from global memory (L2; the block was copied one step ago).
+//      -> S(ys), ys = row - r; snr = R(ys)/sqrt(S), stats.  The h values of a
+//      segment stay in registers for its suffix sums, so each h slot of hE is
+//      free once read: the snr is parked there, and candidates are resolved
+//      once per block.  R(ys) of the first r rows lies in the last r rows of
+//      block k-1, whose buffer is refilled during this pass: the column warps
+//      read those r values first and then release the loader (named barrier 1).
 //      warp 4 meanwhile issues the cp.async copies of block k+1.
 //   One barrier per block publishes the copies and separates the vertical pass
 //   of block k-1 from the horizontal pass of block k; a second one separates
@@ -182,38 +184,38 @@ __global__ void __launch_bounds__(FiltGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
         }
         __syncthreads();
         if (loader) {
-            // ---- the next block's copies while the column warps run the vertical pass
+            // ---- the next block's copies while the column warps run the vertical
+            // pass, once they have read the last r rows of block k-1 (its buffer)
+            asm volatile("bar.sync 1, %0;\n" ::"n"(NT));
             if (k + 1 < k1) load(k + 1, TX, NT - TX);
             cp_async_commit();
         } else if (k < k0) {
+            asm volatile("bar.arrive 1, %0;\n" ::"n"(NT));
             // warm-up block: the suffix sums of its last (2r+1)-row segment
             float acc = 0.f;
 #pragma unroll
             for (int i = L - 1; i >= 1; --i) { acc += hE[((NP - 1) * L + i) * SX + t]; suf[i] = acc; }
         } else {
-            // R(ys) of the rows of block k-1 (ys = ybase - r .. ybase - 1), from
-            // global memory, loaded ahead of the pass
+            // R(ys) of the rows of block k-1 (ys = ybase - r .. ybase - 1): its last
+            // r rows, zero above the image (the copies zero-fill rows outside it)
             float rvp[R];
+            const float* prev = Rb + ((k + 1) & 1) * B * SD + t + A;
 #pragma unroll
-            for (int j = 0; j < R; ++j) {
-                const int ys = ybase + j - R;
-                rvp[j] = (col_s && ys >= 0 && ys < H) ? __ldg(Rimg + (int64_t)ys * W + xs) : 0.f;
-            }
-            // the snr of row j is parked in block k's buffer at row pk(j): the slot
-            // of its own centre value (j >= r, read just before) or one of the last
-            // r rows, which this pass does not read (the next pass reads them from
-            // global memory and the buffer is refilled only after the next barrier)
-            float* park = Rb + (k & 1) * B * SD + t + A;
-            auto pk = [](int j) { return j >= R ? j - R : B - R + j; };
+            for (int j = 0; j < R; ++j) rvp[j] = k > 0 ? prev[(B - R + j) * SD] : 0.f;
+            asm volatile("bar.arrive 1, %0;\n" ::"n"(NT));
+            // the snr of row j is parked in the hE slot of its own h value
+            float* park = hE + t;
             // ---- vertical segment sums -> S for row ys = ybase + j - r
             float s1 = 0.f, s2 = 0.f, cnt = 0.f;
             unsigned cm = 0;
 #pragma unroll
             for (int sgm = 0; sgm < NP; ++sgm) {
+                float hv[L];                    // this segment's h, for its suffix sums
 #pragma unroll
                 for (int o = 0; o < L; ++o) {
                     const int j = sgm * L + o;
                     const float h = hE[j * SX + t];
+                    hv[o] = h;
                     pre = (o == 0) ? h : pre + h;
                     const float Ssum = (o + 1 < L) ? suf[o + 1] + pre : pre;
                     const float S = Ssum * (rowS[j].y * inv_nx);
@@ -226,12 +228,12 @@ __global__ void __launch_bounds__(FiltGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
                     s2 = fmaf(snr, snr, s2);
                     cnt += valid ? 1.f : 0.f;
                     cm |= (valid && snr > a.kappa) ? 1u << j : 0u;
-                    park[pk(j) * SD] = snr;
+                    park[j * SX] = snr;
                 }
-                // suffix sums of the finished segment for the next one (hE is intact)
+                // suffix sums of the finished segment for the next one
                 float acc = 0.f;
 #pragma unroll
-                for (int i = L - 1; i >= 1; --i) { acc += hE[(sgm * L + i) * SX + t]; suf[i] = acc; }
+                for (int i = L - 1; i >= 1; --i) { acc += hv[i]; suf[i] = acc; }
             }
             d1 += s1;
             d2 += s2;
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(FiltGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
                     for (unsigned b = cm; b; b &= b - 1) {
                         const int j = __ffs(b) - 1;
                         ra.xkeys[idx] = ((uint64_t)row << 32) | ((uint64_t)(ybase + j - R) << 16) | (uint64_t)xs;
-                        ra.xvals[idx] = park[pk(j) * SD];
+                        ra.xvals[idx] = park[j * SX];
                         ++idx;
                     }
                 } else {
@@ -268,7 +270,7 @@ __global__ void __launch_bounds__(FiltGeom<R>::NT, 4) k_filter_res(ResArgs ra) {
                         const int j = __ffs(any) - 1;
                         any &= any - 1;
                         const bool cand = (cm >> j) & 1u;
-                        emit_res_candidates<TS>(ra, row, ybase + j - R, xs, cand ? park[pk(j) * SD] : 0.f, cand,
+                        emit_res_candidates<TS>(ra, row, ybase + j - R, xs, cand ? park[j * SX] : 0.f, cand,
                                                 m0, nm);
                     }
                 }
