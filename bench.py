@@ -379,7 +379,7 @@ def measure(lpf, torch, dev, spec, dtype, steps, warmup, pool_n, seed, qc=False,
         T += 1
         if k >= ahead:
             poll()
-    for _ in range(ahead):
+    for _ in range(min(ahead, steps)):     # the frames still unpolled
         poll()
     ev1.record(cur)
     torch.cuda.synchronize()
@@ -788,7 +788,7 @@ def run_stress(args):
         T += 1
         if k >= ahead:
             poll_and_gather()
-    for _ in range(ahead):
+    for _ in range(min(ahead, args.steps)):     # the frames still unpolled
         poll_and_gather()
     ev1.record(cur)
     torch.cuda.synchronize()
