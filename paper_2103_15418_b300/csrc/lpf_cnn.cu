@@ -24,6 +24,8 @@ struct lpf_cnn {
     __nv_bfloat16* act1 = nullptr;    // [max_batch][F/2][Tw/2][16]
     __nv_bfloat16* act2 = nullptr;    // [max_batch][F/4][Tw/4][32]
     unsigned* err = nullptr;          // bit 0: an MMA completion wait ran out
+    int n_sm = 0;
+    bool fused = false;               // 32 x 64 spectra: the one-kernel network
 };
 
 namespace {
@@ -118,6 +120,13 @@ int lpf_cnn_open(lpf_cnn** out, int F, int Tw, const float* params, size_t n_par
     if (rc == LPF_OK) rc = upload<__nv_bfloat16>(&c->act2, nullptr, (size_t)max_batch * (F / 4) * (Tw / 4) * kC2);
     if (rc == LPF_OK) rc = upload<unsigned>(&c->err, nullptr, 1);
     if (rc == LPF_OK && cudaMemset(c->err, 0, sizeof(unsigned)) != cudaSuccess) rc = LPF_E_CUDA;
+    if (rc == LPF_OK && cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess)
+        rc = LPF_E_CUDA;
+    c->fused = F == fused::H0 && Tw == fused::W0;
+    if (rc == LPF_OK && c->fused &&
+        cudaFuncSetAttribute(k_cnn_fused_32x64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused::SMEM) !=
+            cudaSuccess)
+        rc = LPF_E_CUDA;
     if (rc == LPF_OK &&
         (cudaFuncSetAttribute(k_cnn_conv_tc<kC1, kC2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)conv_tc_smem_bytes<kC1, kC2>()) != cudaSuccess ||
@@ -139,6 +148,12 @@ int lpf_cnn_forward(lpf_cnn* c, const float* x_dev, int n, float* out_dev) {
     if (cudaSetDevice(c->dev) != cudaSuccess) return LPF_E_CUDA;
     cudaGetLastError();
     const int F = c->F, Tw = c->Tw;
+    if (c->fused) {
+        const int grid = std::min(n, 2 * c->n_sm);
+        k_cnn_fused_32x64<<<grid, kRows, fused::SMEM, c->st>>>(x_dev, n, c->w1, c->b1, c->w2, c->b2, c->w3, c->b3,
+                                                              c->hw, c->hb, out_dev, c->err);
+        return cudaGetLastError() == cudaSuccess ? LPF_OK : LPF_E_CUDA;
+    }
     const int64_t win1 = (int64_t)n * (F / 2) * (Tw / 2);
     const int g1 = (int)std::min<int64_t>((win1 + 255) / 256, 148 * 16);
     k_cnn_conv1<<<g1, 256, 0, c->st>>>(x_dev, n, F, Tw, c->w1, c->b1, c->act1);

@@ -243,5 +243,246 @@ constexpr size_t conv_tc_smem_bytes() {
     return (size_t)kRows * 9 * CIN * 2 + (size_t)COUT * 9 * CIN * 2;
 }
 
+
+// ---------------------------------------------------------------------------
+// The whole network for 32 x 64 spectra in one persistent kernel: a CTA of 128
+// threads takes one spectrum at a time and keeps every activation in shared
+// memory, so a spectrum costs one 8 KB read and a 20-byte write of HBM.
+//   conv1 (CUDA cores, FP32): thread t computes the 2x2-pooled pixels
+//         (4 j + t / 32, t % 32), j = 0..3, as k_cnn_conv1, into act1.
+//   conv2 (tcgen05): act1 is stored with a zero border as [c / 8][18][34][c % 8]
+//         (16 x 32 pixels + 1 on each side), so the 8 pixels of one image row
+//         and 8 channels are one core matrix.  An output tile of 16 rows x 8
+//         columns (M = 128, row m = 8 y + i) then needs no gathered copy: for
+//         tap (ky, kx) the A operand is the same storage seen from pixel
+//         (ky, 8 q + kx), with 34 pixels between 8-row groups (stride offset)
+//         and the next 8 channels one plane further (leading offset).  Nine
+//         MMAs of 128 x 32 x 16 per tile, four tiles per spectrum.
+//   conv2 epilogue: bias, Leaky ReLU, 2x2 mean over lanes m ^ 1 and m ^ 8, BF16
+//         into act2 stored likewise as [c / 8][18][18][c % 8] (8 x 16 pixels,
+//         a zero border, and 8 more zero rows).
+//   conv3 (tcgen05): an 8 x 16 spectrum is two column halves of 8; each half is
+//         an M = 128 MMA whose first 64 rows are its 8 x 8 pixels and whose
+//         other 64 rows read the zero rows below and are not used (twice the
+//         MMA work of conv3 in exchange for no gather).  2 x 9 taps x 2 K-steps
+//         of 128 x 64 x 16.
+//   conv3 epilogue: warps 0 and 1 hold the 64 + 64 pixels: bias, Leaky ReLU, the
+//         two halves added per thread, the 64 rows summed per channel through
+//         shared memory, the mean, then the head (threads 0..4).
+// Tensor memory: 256 columns per CTA (conv2: 4 x 32, conv3: 2 x 64); two CTAs
+// per SM (about 104 KB of shared memory each) use all 512.
+namespace fused {
+constexpr int H0 = 32, W0 = 64, H1 = 16, W1 = 32, H2 = 8, W2 = 16;
+constexpr int Y1 = H1 + 2, X1 = W1 + 2;          // act1 with its border
+constexpr int Y2 = 18, X2 = W2 + 2;              // act2: border + 8 zero rows
+constexpr int K2 = 9 * kC1, K3 = 9 * kC2;        // 144, 288
+constexpr uint32_t OFF_W2 = 0;
+constexpr uint32_t OFF_W3 = OFF_W2 + kC2 * K2 * 2;             // 9216
+constexpr uint32_t OFF_A1 = OFF_W3 + kC3 * K3 * 2;             // + 36864
+constexpr uint32_t OFF_A2 = OFF_A1 + 2 * Y1 * X1 * 16;         // + 19584
+constexpr uint32_t OFF_ROWS = OFF_A2 + 4 * Y2 * X2 * 16;       // + 20736
+constexpr int RP = kC3 + 1;                                    // row pitch of the channel sums
+constexpr uint32_t SMEM = OFF_ROWS + 64 * RP * 4;              // + 16640
+constexpr uint32_t TCOLS = 256;
+static_assert(OFF_A1 % 128 == 0 && OFF_A2 % 128 == 0 && OFF_ROWS % 16 == 0, "alignment");
+}  // namespace fused
+
+__global__ void __launch_bounds__(kRows, 2) k_cnn_fused_32x64(
+    const float* __restrict__ x, int n, const float* __restrict__ w1, const float* __restrict__ b1,
+    const __nv_bfloat16* __restrict__ wk2, const float* __restrict__ b2, const __nv_bfloat16* __restrict__ wk3,
+    const float* __restrict__ b3, const float* __restrict__ hw, const float* __restrict__ hb,
+    float* __restrict__ res, unsigned* __restrict__ err) {
+    using namespace fused;
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ float sw1[kC1 * 9], sb1[kC1], sfeat[kC3];
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tslot;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if (warp == 0) tc::tmem_alloc(&tslot, TCOLS);
+    if (t == 0) tc::mbar_init(&mbar, 1);
+    for (int i = t; i < kC1 * 9; i += kRows) sw1[i] = w1[i];
+    if (t < kC1) sb1[t] = b1[t];
+    // weights in the K-major core-matrix layout
+    for (int i = t; i < kC2 * (K2 / 8); i += kRows) {
+        const int r = i / (K2 / 8), j = i - r * (K2 / 8);
+        *reinterpret_cast<uint4*>(smem + OFF_W2 + tc::kmajor_offset(r, 8 * j, K2 / 8)) =
+            __ldg(reinterpret_cast<const uint4*>(wk2 + r * K2 + 8 * j));
+    }
+    for (int i = t; i < kC3 * (K3 / 8); i += kRows) {
+        const int r = i / (K3 / 8), j = i - r * (K3 / 8);
+        *reinterpret_cast<uint4*>(smem + OFF_W3 + tc::kmajor_offset(r, 8 * j, K3 / 8)) =
+            __ldg(reinterpret_cast<const uint4*>(wk3 + r * K3 + 8 * j));
+    }
+    // act1 and act2 start zero: borders and spare rows stay zero
+    for (uint32_t o = OFF_A1 + 16 * t; o < OFF_ROWS; o += 16 * kRows)
+        *reinterpret_cast<uint4*>(smem + o) = make_uint4(0u, 0u, 0u, 0u);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = tslot;
+    const uint32_t sbase = tc::smem_u32(smem);
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    float* rows = reinterpret_cast<float*>(smem + OFF_ROWS);
+    bool ok = true;
+    for (int s = blockIdx.x; s < n && ok; s += gridDim.x) {
+        // ---- conv1 -> act1 (interior)
+        const float* xs = x + (int64_t)s * H0 * W0;
+#pragma unroll 1
+        for (int jj = 0; jj < 4; ++jj) {
+            const int py = 4 * jj + warp, px = lane;
+            float p[4][4];
+#pragma unroll
+            for (int dy = 0; dy < 4; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 4; ++dx) {
+                    const int yy = 2 * py - 1 + dy, xx = 2 * px - 1 + dx;
+                    p[dy][dx] = (yy >= 0 && yy < H0 && xx >= 0 && xx < W0) ? __ldg(xs + yy * W0 + xx) : 0.f;
+                }
+            uint32_t packed[kC1 / 2];
+#pragma unroll
+            for (int c = 0; c < kC1; ++c) {
+                float v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int oy = q >> 1, ox = q & 1;
+                    float acc = sb1[c];
+#pragma unroll
+                    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                        for (int kx = 0; kx < 3; ++kx) acc = fmaf(sw1[c * 9 + ky * 3 + kx], p[oy + ky][ox + kx], acc);
+                    v[q] = leaky(acc);
+                }
+                const float m = ((v[0] + v[1]) + (v[2] + v[3])) * 0.25f;
+                const __nv_bfloat16 h = __float2bfloat16_rn(m);
+                const uint16_t u = *reinterpret_cast<const uint16_t*>(&h);
+                if (c & 1) packed[c >> 1] |= (uint32_t)u << 16;
+                else packed[c >> 1] = u;
+            }
+#pragma unroll
+            for (int cg = 0; cg < 2; ++cg)
+                *reinterpret_cast<uint4*>(smem + OFF_A1 + ((cg * Y1 + py + 1) * X1 + px + 1) * 16) =
+                    make_uint4(packed[4 * cg], packed[4 * cg + 1], packed[4 * cg + 2], packed[4 * cg + 3]);
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        // ---- conv2: 4 tiles x 9 taps, A read in place from act1
+        if (t == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(kRows, kC2);
+#pragma unroll 1
+            for (int q = 0; q < 4; ++q)
+#pragma unroll 1
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int ky = tap / 3, kx = tap - 3 * ky;
+                    const uint64_t ad = tc::smem_desc(sbase + OFF_A1 + (ky * X1 + 8 * q + kx) * 16, Y1 * X1 * 16, X1 * 16);
+                    const uint64_t bd = tc::smem_desc(sbase + OFF_W2 + 256 * tap, 128, (K2 / 8) * 128);
+                    tc::mma_bf16(taddr + 32 * q, ad, bd, idesc, tap > 0 ? 1u : 0u);
+                }
+            tc::mma_commit(&mbar);
+        }
+        bool done = tc::mbar_wait(&mbar, 0, kWaitNs);
+        tc::fence_after_sync();
+        if (!__syncthreads_and(done)) {
+            if (t == 0) atomicOr(err, 1u);
+            tc::mbar_wait(&mbar, 0, kWaitNs);     // the MMAs still in flight, bounded
+            ok = false;
+            break;
+        }
+        // ---- conv2 epilogue: row m = 32 warp + lane = 8 y + i of tile q
+        {
+            const int m = 32 * warp + lane, y = m >> 3, i = m & 7;
+            const bool keep = ((y | i) & 1) == 0;
+#pragma unroll 1
+            for (int q = 0; q < 4; ++q) {
+                float v[32];
+                tc::tmem_ld32(taddr + lane_off + 32 * q, v);
+                uint32_t packed[16];
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    float h = leaky(v[c] + __ldg(b2 + c));
+                    h += __shfl_xor_sync(0xffffffffu, h, 1);
+                    h += __shfl_xor_sync(0xffffffffu, h, 8);
+                    const __nv_bfloat16 bh = __float2bfloat16_rn(h * 0.25f);
+                    const uint16_t u = *reinterpret_cast<const uint16_t*>(&bh);
+                    if (c & 1) packed[c >> 1] |= (uint32_t)u << 16;
+                    else packed[c >> 1] = u;
+                }
+                if (keep) {
+                    const int pr = y >> 1, pc = 4 * q + (i >> 1);
+#pragma unroll
+                    for (int cg = 0; cg < 4; ++cg)
+                        *reinterpret_cast<uint4*>(smem + OFF_A2 + ((cg * Y2 + pr + 1) * X2 + pc + 1) * 16) =
+                            make_uint4(packed[4 * cg], packed[4 * cg + 1], packed[4 * cg + 2], packed[4 * cg + 3]);
+                }
+            }
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        // ---- conv3: two column halves x 9 taps x 2 K-steps
+        if (t == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(kRows, kC3);
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h)
+#pragma unroll 1
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int ky = tap / 3, kx = tap - 3 * ky;
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint64_t ad = tc::smem_desc(
+                            sbase + OFF_A2 + ((2 * ks * Y2 + ky) * X2 + 8 * h + kx) * 16, Y2 * X2 * 16, X2 * 16);
+                        const uint64_t bd =
+                            tc::smem_desc(sbase + OFF_W3 + (4 * tap + 2 * ks) * 128, 128, (K3 / 8) * 128);
+                        tc::mma_bf16(taddr + 128 + 64 * h, ad, bd, idesc, (tap | ks) ? 1u : 0u);
+                    }
+                }
+            tc::mma_commit(&mbar);
+        }
+        done = tc::mbar_wait(&mbar, 1, kWaitNs);
+        tc::fence_after_sync();
+        if (!__syncthreads_and(done)) {
+            if (t == 0) atomicOr(err, 1u);
+            tc::mbar_wait(&mbar, 1, kWaitNs);     // the MMAs still in flight, bounded
+            ok = false;
+            break;
+        }
+        // ---- conv3 epilogue: warps 0 and 1 (rows 0..63 = pixel (m / 8, 8 h + m % 8))
+        if (warp < 2) {
+            const int m = 32 * warp + lane;
+#pragma unroll 1
+            for (int c0 = 0; c0 < kC3; c0 += 32) {
+                float vl[32], vr[32];
+                tc::tmem_ld32(taddr + lane_off + 128 + c0, vl);
+                tc::tmem_ld32(taddr + lane_off + 192 + c0, vr);
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const float bc = __ldg(b3 + c0 + c);
+                    rows[m * RP + c0 + c] = leaky(vl[c] + bc) + leaky(vr[c] + bc);
+                }
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        if (t < kC3) {
+            float acc = 0.f;
+            for (int m = 0; m < 64; ++m) acc += rows[m * RP + t];
+            sfeat[t] = acc * (1.0f / (H2 * W2));
+        }
+        __syncthreads();
+        if (t < kOut) {
+            float z = __ldg(hb + t);
+            for (int c = 0; c < kC3; ++c) z = fmaf(__ldg(hw + t * kC3 + c), sfeat[c], z);
+            res[(int64_t)s * kOut + t] = (t == 2 || t == 4) ? expf(z) : z;
+        }
+        // the next spectrum's conv1 writes only act1, read by no one until its MMAs
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, TCOLS);
+}
+
 }  // namespace cnn
 }  // namespace lpf

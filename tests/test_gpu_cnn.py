@@ -50,6 +50,26 @@ def test_cnn_matches_oracle(lib, F, Tw, n):
     assert np.ptp(ref[:, 0]) > 10 * ATOL or n == 1                  # the inputs move the outputs
 
 
+def test_cnn_batch_spans_many_spectra_per_cta(lib):
+    """700 spectra of 32 x 64: more than one spectrum per CTA of the one-kernel
+    network (at most two CTAs per SM).  Sampled spectra from every position of the
+    persistent loop against the oracle, a repeat bit-identical, and a spectrum's
+    outputs independent of the batch it is in."""
+    params = synth.cnn_params(7)
+    n = 700
+    x = spectra(n, 32, 64, seed=5)
+    with lib.Cnn(32, 64, params, max_batch=n) as net:
+        got = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+        again = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+        part = net.forward(torch.from_numpy(x[290:330].copy()).cuda()).cpu().numpy()
+    np.testing.assert_array_equal(got, again)
+    np.testing.assert_array_equal(got[290:330], part)
+    idx = [0, 1, 147, 148, 295, 296, 297, 443, 591, 592, 593, 699]
+    ref = C.forward(x[idx].astype(np.float64), params)
+    np.testing.assert_allclose(got[idx], ref, rtol=RTOL, atol=ATOL)
+    assert np.all(np.isfinite(got))
+
+
 def test_cnn_on_gathered_dynamic_spectra(lib):
     """The network as the consumer of the dynamic-spectrum gather: the candidates
     of a tiny stream, their 8 x 16 spectra gathered on the GPU, then the network."""
