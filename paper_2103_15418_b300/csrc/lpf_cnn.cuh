@@ -247,9 +247,13 @@ constexpr size_t conv_tc_smem_bytes() {
 // ---------------------------------------------------------------------------
 // The whole network for 32 x 64 spectra in one persistent kernel: a CTA of 128
 // threads takes one spectrum at a time and keeps every activation in shared
-// memory, so a spectrum costs one 8 KB read and a 20-byte write of HBM.
+// memory, so a spectrum costs one 8 KB read and a 20-byte write of HBM.  The
+// next spectrum's input is copied in (cp.async) while the tensor cores work on
+// the current one.
 //   conv1 (CUDA cores, FP32): thread t computes the 2x2-pooled pixels
-//         (4 j + t / 32, t % 32), j = 0..3, as k_cnn_conv1, into act1.
+//         (4 j + t / 32, t % 32), j = 0..3; the two horizontally adjacent
+//         outputs of a window share every weight, so they are one packed FP32x2
+//         FMA chain (each lane rounds like the scalar chain of k_cnn_conv1).
 //   conv2 (tcgen05): act1 is stored with a zero border as [c / 8][18][34][c % 8]
 //         (16 x 32 pixels + 1 on each side), so the 8 pixels of one image row
 //         and 8 channels are one core matrix.  An output tile of 16 rows x 8
@@ -268,9 +272,10 @@ constexpr size_t conv_tc_smem_bytes() {
 //         of 128 x 64 x 16.
 //   conv3 epilogue: warps 0 and 1 hold the 64 + 64 pixels: bias, Leaky ReLU, the
 //         two halves added per thread, the 64 rows summed per channel through
-//         shared memory, the mean, then the head (threads 0..4).
+//         shared memory (over act1, whose border is zeroed again afterwards),
+//         the mean, then the head (threads 0..4).
 // Tensor memory: 256 columns per CTA (conv2: 4 x 32, conv3: 2 x 64); two CTAs
-// per SM (about 104 KB of shared memory each) use all 512.
+// per SM use all 512.
 namespace fused {
 constexpr int H0 = 32, W0 = 64, H1 = 16, W1 = 32, H2 = 8, W2 = 16;
 constexpr int Y1 = H1 + 2, X1 = W1 + 2;          // act1 with its border
@@ -280,12 +285,23 @@ constexpr uint32_t OFF_W2 = 0;
 constexpr uint32_t OFF_W3 = OFF_W2 + kC2 * K2 * 2;             // 9216
 constexpr uint32_t OFF_A1 = OFF_W3 + kC3 * K3 * 2;             // + 36864
 constexpr uint32_t OFF_A2 = OFF_A1 + 2 * Y1 * X1 * 16;         // + 19584
-constexpr uint32_t OFF_ROWS = OFF_A2 + 4 * Y2 * X2 * 16;       // + 20736
-constexpr int RP = kC3 + 1;                                    // row pitch of the channel sums
-constexpr uint32_t SMEM = OFF_ROWS + 64 * RP * 4;              // + 16640
+constexpr uint32_t OFF_X = OFF_A2 + 4 * Y2 * X2 * 16;          // + 20736
+constexpr uint32_t SMEM = OFF_X + H0 * W0 * 4;                 // + 8192
+constexpr int RP = kC3 + 1;                                    // row pitch of the channel sums (in act1)
 constexpr uint32_t TCOLS = 256;
-static_assert(OFF_A1 % 128 == 0 && OFF_A2 % 128 == 0 && OFF_ROWS % 16 == 0, "alignment");
+static_assert(OFF_A1 % 128 == 0 && OFF_A2 % 128 == 0 && OFF_X % 16 == 0, "alignment");
+static_assert(64 * RP * 4 <= 2 * Y1 * X1 * 16, "channel sums fit in act1");
 }  // namespace fused
+
+// the input spectrum s (8 KB) into shared memory, 16 bytes per copy
+__device__ __forceinline__ void cnn_fetch_spectrum(uint8_t* dst, const float* x, int s) {
+    const char* src = reinterpret_cast<const char*>(x + (int64_t)s * fused::H0 * fused::W0);
+    for (int i = threadIdx.x; i < fused::H0 * fused::W0 / 4; i += kRows) {
+        const uint32_t d = tc::smem_u32(dst + 16 * i);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src + 16 * i));
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+}
 
 __global__ void __launch_bounds__(kRows, 2) k_cnn_fused_32x64(
     const float* __restrict__ x, int n, const float* __restrict__ w1, const float* __restrict__ b1,
@@ -294,14 +310,20 @@ __global__ void __launch_bounds__(kRows, 2) k_cnn_fused_32x64(
     float* __restrict__ res, unsigned* __restrict__ err) {
     using namespace fused;
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ float sw1[kC1 * 9], sb1[kC1], sfeat[kC3];
+    __shared__ float2 sw1[kC1 * 9];                  // conv1 weights, each twice (packed FMA operand)
+    __shared__ float sb1[kC1], sb2[kC2], sb3[kC3], shw[kOut * kC3], shb[kOut], sfeat[kC3];
     __shared__ uint64_t mbar;
     __shared__ uint32_t tslot;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if ((int)blockIdx.x < n) cnn_fetch_spectrum(smem + OFF_X, x, blockIdx.x);
     if (warp == 0) tc::tmem_alloc(&tslot, TCOLS);
     if (t == 0) tc::mbar_init(&mbar, 1);
-    for (int i = t; i < kC1 * 9; i += kRows) sw1[i] = w1[i];
+    for (int i = t; i < kC1 * 9; i += kRows) sw1[i] = make_float2(w1[i], w1[i]);
+    for (int i = t; i < kOut * kC3; i += kRows) shw[i] = hw[i];
     if (t < kC1) sb1[t] = b1[t];
+    if (t < kC2) sb2[t] = b2[t];
+    if (t < kC3) sb3[t] = b3[t];
+    if (t < kOut) shb[t] = hb[t];
     // weights in the K-major core-matrix layout
     for (int i = t; i < kC2 * (K2 / 8); i += kRows) {
         const int r = i / (K2 / 8), j = i - r * (K2 / 8);
@@ -314,7 +336,7 @@ __global__ void __launch_bounds__(kRows, 2) k_cnn_fused_32x64(
             __ldg(reinterpret_cast<const uint4*>(wk3 + r * K3 + 8 * j));
     }
     // act1 and act2 start zero: borders and spare rows stay zero
-    for (uint32_t o = OFF_A1 + 16 * t; o < OFF_ROWS; o += 16 * kRows)
+    for (uint32_t o = OFF_A1 + 16 * t; o < OFF_X; o += 16 * kRows)
         *reinterpret_cast<uint4*>(smem + o) = make_uint4(0u, 0u, 0u, 0u);
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -323,37 +345,43 @@ __global__ void __launch_bounds__(kRows, 2) k_cnn_fused_32x64(
     const uint32_t taddr = tslot;
     const uint32_t sbase = tc::smem_u32(smem);
     const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-    float* rows = reinterpret_cast<float*>(smem + OFF_ROWS);
+    const float* sx = reinterpret_cast<const float*>(smem + OFF_X);
+    float* rows = reinterpret_cast<float*>(smem + OFF_A1);
     bool ok = true;
     for (int s = blockIdx.x; s < n && ok; s += gridDim.x) {
-        // ---- conv1 -> act1 (interior)
-        const float* xs = x + (int64_t)s * H0 * W0;
+        asm volatile("cp.async.wait_group 0;\n" ::);
+        __syncthreads();
+        // ---- conv1 -> act1 (interior), from the spectrum in shared memory
 #pragma unroll 1
         for (int jj = 0; jj < 4; ++jj) {
             const int py = 4 * jj + warp, px = lane;
-            float p[4][4];
+            // P[r][k] = (p[r][k], p[r][k + 1]): the inputs of the left and right output
+            float2 P[4][3];
 #pragma unroll
-            for (int dy = 0; dy < 4; ++dy)
+            for (int dy = 0; dy < 4; ++dy) {
+                const int yy = 2 * py - 1 + dy;
+                float p[4];
 #pragma unroll
                 for (int dx = 0; dx < 4; ++dx) {
-                    const int yy = 2 * py - 1 + dy, xx = 2 * px - 1 + dx;
-                    p[dy][dx] = (yy >= 0 && yy < H0 && xx >= 0 && xx < W0) ? __ldg(xs + yy * W0 + xx) : 0.f;
+                    const int xx = 2 * px - 1 + dx;
+                    p[dx] = (yy >= 0 && yy < H0 && xx >= 0 && xx < W0) ? sx[yy * W0 + xx] : 0.f;
                 }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) P[dy][k] = make_float2(p[k], p[k + 1]);
+            }
             uint32_t packed[kC1 / 2];
 #pragma unroll
             for (int c = 0; c < kC1; ++c) {
-                float v[4];
+                float2 a[2];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int oy = q >> 1, ox = q & 1;
-                    float acc = sb1[c];
+                for (int oy = 0; oy < 2; ++oy) {
+                    a[oy] = make_float2(sb1[c], sb1[c]);
 #pragma unroll
                     for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
-                        for (int kx = 0; kx < 3; ++kx) acc = fmaf(sw1[c * 9 + ky * 3 + kx], p[oy + ky][ox + kx], acc);
-                    v[q] = leaky(acc);
+                        for (int kx = 0; kx < 3; ++kx) a[oy] = __ffma2_rn(sw1[c * 9 + ky * 3 + kx], P[oy + ky][kx], a[oy]);
                 }
-                const float m = ((v[0] + v[1]) + (v[2] + v[3])) * 0.25f;
+                const float m = ((leaky(a[0].x) + leaky(a[0].y)) + (leaky(a[1].x) + leaky(a[1].y))) * 0.25f;
                 const __nv_bfloat16 h = __float2bfloat16_rn(m);
                 const uint16_t u = *reinterpret_cast<const uint16_t*>(&h);
                 if (c & 1) packed[c >> 1] |= (uint32_t)u << 16;
@@ -368,12 +396,14 @@ __global__ void __launch_bounds__(kRows, 2) k_cnn_fused_32x64(
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
+        // the next spectrum's input, behind the tensor-core work on this one
+        if (s + (int)gridDim.x < n) cnn_fetch_spectrum(smem + OFF_X, x, s + gridDim.x);
         // ---- conv2: 4 tiles x 9 taps, A read in place from act1
         if (t == 0) {
             constexpr uint32_t idesc = tc::idesc_bf16_f32(kRows, kC2);
 #pragma unroll 1
             for (int q = 0; q < 4; ++q)
-#pragma unroll 1
+#pragma unroll
                 for (int tap = 0; tap < 9; ++tap) {
                     const int ky = tap / 3, kx = tap - 3 * ky;
                     const uint64_t ad = tc::smem_desc(sbase + OFF_A1 + (ky * X1 + 8 * q + kx) * 16, Y1 * X1 * 16, X1 * 16);
@@ -401,7 +431,7 @@ __global__ void __launch_bounds__(kRows, 2) k_cnn_fused_32x64(
                 uint32_t packed[16];
 #pragma unroll
                 for (int c = 0; c < 32; ++c) {
-                    float h = leaky(v[c] + __ldg(b2 + c));
+                    float h = leaky(v[c] + sb2[c]);
                     h += __shfl_xor_sync(0xffffffffu, h, 1);
                     h += __shfl_xor_sync(0xffffffffu, h, 8);
                     const __nv_bfloat16 bh = __float2bfloat16_rn(h * 0.25f);
@@ -427,7 +457,7 @@ __global__ void __launch_bounds__(kRows, 2) k_cnn_fused_32x64(
             constexpr uint32_t idesc = tc::idesc_bf16_f32(kRows, kC3);
 #pragma unroll 1
             for (int h = 0; h < 2; ++h)
-#pragma unroll 1
+#pragma unroll
                 for (int tap = 0; tap < 9; ++tap) {
                     const int ky = tap / 3, kx = tap - 3 * ky;
 #pragma unroll
@@ -449,7 +479,8 @@ __global__ void __launch_bounds__(kRows, 2) k_cnn_fused_32x64(
             ok = false;
             break;
         }
-        // ---- conv3 epilogue: warps 0 and 1 (rows 0..63 = pixel (m / 8, 8 h + m % 8))
+        // ---- conv3 epilogue: warps 0 and 1 (rows 0..63 = pixel (m / 8, 8 h + m % 8));
+        // act1 is free (the conv2 MMAs have completed) and takes the channel sums
         if (warp < 2) {
             const int m = 32 * warp + lane;
 #pragma unroll 1
@@ -459,7 +490,7 @@ __global__ void __launch_bounds__(kRows, 2) k_cnn_fused_32x64(
                 tc::tmem_ld32(taddr + lane_off + 192 + c0, vr);
 #pragma unroll
                 for (int c = 0; c < 32; ++c) {
-                    const float bc = __ldg(b3 + c0 + c);
+                    const float bc = sb3[c0 + c];
                     rows[m * RP + c0 + c] = leaky(vl[c] + bc) + leaky(vr[c] + bc);
                 }
             }
@@ -473,12 +504,18 @@ __global__ void __launch_bounds__(kRows, 2) k_cnn_fused_32x64(
         }
         __syncthreads();
         if (t < kOut) {
-            float z = __ldg(hb + t);
-            for (int c = 0; c < kC3; ++c) z = fmaf(__ldg(hw + t * kC3 + c), sfeat[c], z);
+            float z = shb[t];
+            for (int c = 0; c < kC3; ++c) z = fmaf(shw[t * kC3 + c], sfeat[c], z);
             res[(int64_t)s * kOut + t] = (t == 2 || t == 4) ? expf(z) : z;
         }
-        // the next spectrum's conv1 writes only act1, read by no one until its MMAs
+        // act1 again: zero its border (the next conv1 writes the interior)
+        for (int i = t; i < 2 * Y1 * X1; i += kRows) {
+            const int cg = i / (Y1 * X1), r = i - cg * (Y1 * X1), yy = r / X1, xx = r - yy * X1;
+            if (yy == 0 || yy == Y1 - 1 || xx == 0 || xx == X1 - 1)
+                *reinterpret_cast<uint4*>(smem + OFF_A1 + i * 16) = make_uint4(0u, 0u, 0u, 0u);
+        }
     }
+    asm volatile("cp.async.wait_group 0;\n" ::);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(taddr, TCOLS);
