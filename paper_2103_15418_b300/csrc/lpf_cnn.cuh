@@ -22,6 +22,8 @@
 //   conv3: rows are ordered (spectrum, pixel) and a spectrum's pixels are a
 //          whole number of rows per tile; their mean goes through shared
 //          memory, and the head follows in the same CTA.
+// For 32 x 64 spectra the whole network runs instead as one persistent kernel
+// with the activations in shared memory (k_cnn_fused_32x64, at the end).
 #pragma once
 #include "lpf_tc.cuh"
 

@@ -38,7 +38,11 @@ def test_stress_sampled_trials_and_dynspec(lib, capsys):
             _, c, n, trunc = s.poll(timeout_ms=120000)
         assert not trunc
         assert_sorted_unique(c)
-        dms = [0, 1, 400, 1000]
+        # trials with candidates (the two with the most) beside fixed ones, so that the
+        # comparisons below cover crossings and not only empty trials
+        counts = np.bincount(np.asarray(c["dm_idx"], dtype=np.int64), minlength=len(spec.dm_grid)) if len(c) else []
+        busy = [int(d) for d in np.argsort(-np.asarray(counts))[:2] if len(c) and counts[d] > 0]
+        dms = sorted(set([0, 1, 400, 1000] + busy))
         compare_storage(c, frame_at, T, delays, spec.box_r, spec.kappa, "fp16", dms=dms,
                         gpu_stats=s.stats(), res_at=res_at)
         # precision report against the oracle on the unrounded frames
@@ -46,6 +50,7 @@ def test_stress_sampled_trials_and_dynspec(lib, capsys):
         with capsys.disabled():
             print("\nPRECISION_REPORT " + json.dumps({"stress-2048x2048-32sb-1001dm-depth114": {"fp16": rep}}))
         assert rep["sym_diff"] == 0 and rep["max_rel_snr_err"] <= SNR_RTOL["fp16"], rep
+        assert not busy or rep["matched"] > 0, rep
         Tw = 64
         ds = s.dynspec(c, Tw)                              # contiguous [n][32][64] FP32 batch
         assert ds.shape == (len(c), 32, Tw) and ds.is_contiguous()
