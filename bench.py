@@ -354,7 +354,7 @@ def measure(lpf, torch, dev, spec, dtype, steps, warmup, pool_n, seed, qc=False,
         s.push(pool_dev[T % pool_n], T)
 
     def poll():
-        _, c, n, _ = s.poll(timeout_ms=600000)
+        _, c, n, _ = s.poll(timeout_ms=600000, copy=False)   # records read in place
         polled.append(n)
 
     for _ in range(spec.depth + warmup):
@@ -373,12 +373,17 @@ def measure(lpf, torch, dev, spec, dtype, steps, warmup, pool_n, seed, qc=False,
     # end-to-end loop below
     ahead = max(1, RESULT_SLOTS - 1)
     out["t_wall0"] = time.time()
+    host = [0.0, 0.0]                        # host seconds in push and poll calls
     ev0.record(cur)
     for k in range(steps):
+        h0 = time.perf_counter()
         push(T)
+        h1 = time.perf_counter()
         T += 1
         if k >= ahead:
             poll()
+        host[0] += h1 - h0
+        host[1] += time.perf_counter() - h1
     for _ in range(min(ahead, steps)):     # the frames still unpolled
         poll()
     ev1.record(cur)
@@ -386,6 +391,7 @@ def measure(lpf, torch, dev, spec, dtype, steps, warmup, pool_n, seed, qc=False,
     out["t_wall1"] = time.time()
     s.set_profiling(False)
     out["elapsed"] = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dist, dev)
+    out["host_ms"] = {"push": 1e3 * host[0] / steps, "poll": 1e3 * host[1] / steps}
     kt = s.kernel_times(reset=True)
     out["per_push"] = {n: kt[n][0] / max(kt[n][1], 1) for n in kt}
     out["ncand"] = float(np.mean(polled[-steps:]))
@@ -398,7 +404,7 @@ def measure(lpf, torch, dev, spec, dtype, steps, warmup, pool_n, seed, qc=False,
         inflight = max(1, RESULT_SLOTS - 1)
 
         def poll_host():
-            Tp, c, n, _ = s.poll(timeout_ms=600000)
+            Tp, c, n, _ = s.poll(timeout_ms=600000, copy=False)
             e2e_cands.append(n)
             lat.append(time.perf_counter() - t_push.pop(Tp))
 
@@ -415,6 +421,17 @@ def measure(lpf, torch, dev, spec, dtype, steps, warmup, pool_n, seed, qc=False,
         out["e2e_s"] = max_over_ranks(time.perf_counter() - t_e0, dist, dev)
         out["lat"], out["e2e_cands"] = lat, e2e_cands
         out["t_wall1e"] = time.time()
+        # the host link alone: pinned frame -> device, CUDA events, 10 copies
+        dst = torch.empty_like(pool_dev[0])
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(cur):
+            dst.copy_(pool_pin[0], non_blocking=True)
+            c0.record(cur)
+            for _ in range(10):
+                dst.copy_(pool_pin[0], non_blocking=True)
+            c1.record(cur)
+        torch.cuda.synchronize()
+        out["h2d_gbs"] = 10 * dst.numel() * dst.element_size() / (c0.elapsed_time(c1) / 1e3) / 1e9
     s.close()
     return out
 
@@ -538,12 +555,16 @@ def run_ours(args):
         "rooflines": rooflines,
         "kernel_ms_per_step": per_push,
         "candidates_per_step": m["ncand"],
+        "host_ms_per_step": m["host_ms"],
         "clocks": clocks.summary(m["t_wall0"], m["t_wall1"]),
     }
     if e2e_value is not None:
         line["e2e"] = {"value": e2e_value, "unit": METRIC,
                        "h2d_bytes_per_step": spec.F * spec.H * spec.W * 4,
-                       "d2h_bytes_per_step": int(np.mean(m["e2e_cands"]) * 24 + spec.n_dm * 16)}
+                       "d2h_bytes_per_step": int(np.mean(m["e2e_cands"]) * 24 + spec.n_dm * 16),
+                       "h2d_link_gbs": m["h2d_gbs"],
+                       "note": "frames are uploaded while earlier ones are searched: a step takes the "
+                               "longer of the search and the upload over the host link"}
         line["latency_ms"] = {"p50": 1e3 * float(np.percentile(m["lat"], 50)),
                               "p99": 1e3 * float(np.percentile(m["lat"], 99)),
                               "what": f"push_frame_host -> poll of the same frame, up to {RESULT_SLOTS} "
@@ -555,6 +576,7 @@ def run_ours(args):
                         "speedup_vs_fp32": ms_step / ms16,
                         "roofline": path_roofline(sp16, "fp16", f16["delays"], ms16, hbm_peak, peak_src),
                         "kernel_ms_per_step": f16["per_push"], "candidates_per_step": f16["ncand"],
+                        "host_ms_per_step": f16["host_ms"],
                         "clocks": clocks.summary(f16["t_wall0"], f16["t_wall1"])}
     if serving is not None:
         line["serving"] = serving

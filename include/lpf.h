@@ -386,8 +386,12 @@ int lpf_cnn_open(lpf_cnn** out, int F, int Tw, const float* params, size_t n_par
                  void* cuda_stream);
 
 /* out_dev [n][5] (FP32, DEVICE) for the spectra x_dev [n][F][Tw] (FP32, DEVICE),
- * n <= max_batch; asynchronous on the network's stream.  Errors: LPF_E_ARG,
- * LPF_E_CUDA. */
+ * n <= max_batch; asynchronous on the network's stream.  32 x 64 spectra run
+ * as one persistent kernel with the activations in shared memory, which copies
+ * each spectrum in 16-byte pieces: x_dev must then be 16-byte aligned (LPF_E_ARG
+ * otherwise).  Other shapes run as three kernels through global memory.  Both
+ * follow the same rounding points (BF16 activations after conv1 and conv2);
+ * their FP32 sums may differ in order.  Errors: LPF_E_ARG, LPF_E_CUDA. */
 int lpf_cnn_forward(lpf_cnn* net, const float* x_dev, int n, float* out_dev);
 
 /* Wait for the network's work; LPF_E_TIMEOUT if a tensor-core completion wait

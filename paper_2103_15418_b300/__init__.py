@@ -258,8 +258,10 @@ class Stream:
         ptr = _host_frame_ptr(frame, self.F * self.H * self.W)
         _check(load().lpf_push_frame_host(self._h, c_void_p(ptr), int(T)), "lpf_push_frame_host")
 
-    def poll(self, cap: Optional[int] = None, timeout_ms: int = -1):
-        """Candidates of the oldest unpolled frame: (T, records, n_found, truncated)."""
+    def poll(self, cap: Optional[int] = None, timeout_ms: int = -1, copy: bool = True):
+        """Candidates of the oldest unpolled frame: (T, records, n_found, truncated).
+        copy=False returns a view of the stream's page-locked record buffer instead
+        of a copy; it is overwritten by the next poll."""
         cap = self._cap if cap is None else int(cap)
         buf = self._out if cap <= self._out.size else np.zeros(cap, dtype=CANDIDATE_DTYPE)
         n = c_int(0)
@@ -269,7 +271,7 @@ class Stream:
         if rc not in (LPF_OK, LPF_E_TRUNCATED):
             raise LpfError(rc, "lpf_poll_candidates")
         k = min(n.value, cap, self._cap)
-        return T.value, buf[:k].copy(), n.value, rc == LPF_E_TRUNCATED
+        return T.value, (buf[:k].copy() if copy else buf[:k]), n.value, rc == LPF_E_TRUNCATED
 
     def dynspec(self, cands, Tw: int, out=None, sync: bool = True):
         """FP32 CUDA tensor [n, F, Tw] of the candidates' dynamic spectra (last polled frame).

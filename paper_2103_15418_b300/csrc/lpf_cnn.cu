@@ -4,6 +4,7 @@
 #include "lpf_cnn.cuh"
 
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -149,6 +150,7 @@ int lpf_cnn_forward(lpf_cnn* c, const float* x_dev, int n, float* out_dev) {
     cudaGetLastError();
     const int F = c->F, Tw = c->Tw;
     if (c->fused) {
+        if (reinterpret_cast<uintptr_t>(x_dev) & 15u) return LPF_E_ARG;   // 16-byte copies of each spectrum
         const int grid = std::min(n, 2 * c->n_sm);
         k_cnn_fused_32x64<<<grid, kRows, fused::SMEM, c->st>>>(x_dev, n, c->w1, c->b1, c->w2, c->b2, c->w3, c->b3,
                                                               c->hw, c->hb, out_dev, c->err);

@@ -97,3 +97,10 @@ def test_cnn_batch_limits(lib):
             net.forward(torch.zeros((5, 8, 16), device="cuda"))
         out = net.forward(torch.zeros((0, 8, 16), device="cuda"))
         assert out.shape == (0, 5)
+    # the one-kernel network copies each 32 x 64 spectrum in 16-byte pieces: a
+    # misaligned batch is refused before any work is enqueued
+    with lib.Cnn(32, 64, params, max_batch=2) as net:
+        buf = torch.zeros(2 * 32 * 64 + 1, device="cuda")
+        with pytest.raises(lib.LpfError):
+            net.forward(buf[1:].view(2, 32, 64))
+        assert np.all(np.isfinite(net.forward(buf[:-1].view(2, 32, 64)).cpu().numpy()))
