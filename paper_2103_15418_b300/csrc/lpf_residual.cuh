@@ -86,12 +86,14 @@ __global__ void __launch_bounds__(ResGeom<R>::NT) k_residual(const float* __rest
         float(*cur)[SD] = Xb[k & 1];
         float(*prev)[SD] = Xb[(k + 1) & 1];
         if (t < WD) {
+            // every load of the block first, then the rounding to the storage type:
+            // all B loads are in flight at once for any TS
             const float* src = X + (int64_t)ybase * W + xl;
+            float xv[B];
 #pragma unroll
-            for (int j = 0; j < B; ++j) {
-                cur[j][t] = (lcol && ybase + j < H) ? as_stored<TS>(__ldg(src)) : 0.f;
-                src += W;
-            }
+            for (int j = 0; j < B; ++j) xv[j] = (lcol && ybase + j < H) ? __ldg(src + (int64_t)j * W) : 0.f;
+#pragma unroll
+            for (int j = 0; j < B; ++j) cur[j][t] = as_stored<TS>(xv[j]);
         }
         if (t < B) rowC[t] = row_count<R>(ybase + t - R, H);
         __syncthreads();
