@@ -189,6 +189,9 @@ __device__ __forceinline__ void d_points(const ResArgs& ra, int row, int ys, int
         in[k] = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
         off[k] = in[k] ? (int64_t)yy * a.W + xx : 0;
     }
+    // unrolled by 4: the loads of four subbands are in flight together (the sum
+    // still runs f = 0, 1, ... in order)
+#pragma unroll 4
     for (int f = 0; f < ra.F; ++f) {
         int slot = ra.Tmod - (int)__ldg(lr + f);
         if (slot < 0) slot += ra.depth;
