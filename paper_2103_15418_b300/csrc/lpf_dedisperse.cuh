@@ -79,8 +79,21 @@ __device__ __forceinline__ float2 to_float2(unsigned u, const __nv_bfloat16*) {
     return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
 }
 
-// 16-bit storage: 8 pixels per thread, plane values kept packed and widened to
-// FP32 when summed (same order, same FP32 arithmetic as above).
+// x += the two 16-bit values of u (low half into x, high half into y) by the
+// mixed-precision add: the 16-bit operand is widened exactly, so each result is
+// the FP32 sum rounded once, as a widening followed by an FP32 add
+__device__ __forceinline__ void add_pair(unsigned u, float& x, float& y, const __half*) {
+    asm("{\n.reg .b16 lo, hi;\nmov.b32 {lo, hi}, %2;\nadd.rn.f32.f16 %0, lo, %0;\nadd.rn.f32.f16 %1, hi, %1;\n}"
+        : "+f"(x), "+f"(y) : "r"(u));
+}
+__device__ __forceinline__ void add_pair(unsigned u, float& x, float& y, const __nv_bfloat16*) {
+    asm("{\n.reg .b16 lo, hi;\nmov.b32 {lo, hi}, %2;\nadd.rn.f32.bf16 %0, lo, %0;\nadd.rn.f32.bf16 %1, hi, %1;\n}"
+        : "+f"(x), "+f"(y) : "r"(u));
+}
+
+// 16-bit storage: 8 pixels per thread, plane values kept packed; the first
+// subband is widened and every further one added by mixed-precision adds (same
+// order, same FP32 rounding as above).
 template <int FMAX, bool FULL, typename TS>
 __global__ void __launch_bounds__(256) k_dedisperse16(
     const TS* __restrict__ ring, float* __restrict__ D, const int16_t* __restrict__ lag,
@@ -112,8 +125,7 @@ __global__ void __launch_bounds__(256) k_dedisperse16(
         for (int f = 1; f < FMAX; ++f)
             if (FULL || f < F) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    a[k] = __fadd2_rn(a[k], to_float2((&cur[f].x)[k], static_cast<const TS*>(nullptr)));
+                for (int k = 0; k < 4; ++k) add_pair((&cur[f].x)[k], a[k].x, a[k].y, static_cast<const TS*>(nullptr));
             }
         float4* o = reinterpret_cast<float4*>(dst);
         o[0] = make_float4(a[0].x, a[0].y, a[1].x, a[1].y);
