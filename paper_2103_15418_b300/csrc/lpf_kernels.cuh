@@ -37,6 +37,19 @@ __device__ __forceinline__ float4 ld4(const __nv_bfloat16* p) {
 __device__ __forceinline__ float ld1(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ld1(const __half* p) { return __half2float(__ldg(p)); }
 __device__ __forceinline__ float ld1(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+// acc + *p: a 16-bit value is widened exactly inside the mixed-precision add, so
+// the result is the FP32 sum rounded once, as ld1 followed by an FP32 add
+__device__ __forceinline__ float add_ld1(const float* p, float acc) { return acc + __ldg(p); }
+__device__ __forceinline__ float add_ld1(const __half* p, float acc) {
+    float r;
+    asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(r) : "h"(__half_as_ushort(__ldg(p))), "f"(acc));
+    return r;
+}
+__device__ __forceinline__ float add_ld1(const __nv_bfloat16* p, float acc) {
+    float r;
+    asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(r) : "h"(__bfloat16_as_ushort(__ldg(p))), "f"(acc));
+    return r;
+}
 
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 __device__ __forceinline__ void st4(__half* p, float4 v) {

@@ -196,11 +196,10 @@ __device__ __forceinline__ void d_points(const ResArgs& ra, int row, int ys, int
         int slot = ra.Tmod - (int)__ldg(lr + f);
         if (slot < 0) slot += ra.depth;
         const TS* plane = ring + ((int64_t)slot * ra.F + f) * a.P;
+        // a point outside the image reads the plane's first value (off = 0); its
+        // sum is replaced by -inf below
 #pragma unroll
-        for (int k = 0; k < NK; ++k) {
-            const float x = in[k] ? ld1(plane + off[k]) : 0.f;
-            v[k] = (f == 0) ? x : v[k] + x;
-        }
+        for (int k = 0; k < NK; ++k) v[k] = (f == 0) ? ld1(plane + off[k]) : add_ld1(plane + off[k], v[k]);
     }
 #pragma unroll
     for (int k = 0; k < NK; ++k)
