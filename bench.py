@@ -571,10 +571,14 @@ def run_ours(args):
                                       "frames in flight"}
     if f16 is not None:
         sp16 = workload_spec("fp16")
+        # the filter reads the same FP32 R images at either storage type
+        tr16 = ["k_dedisperse_fp16", "k_filter_res"]
+        traffic16 = sum(traffic[k] for k in tr16) if all(traffic.get(k) for k in tr16) else None
         ms16 = 1e3 * f16["elapsed"] / args.steps
         line["fp16"] = {"storage": "fp16", "ms_per_step": ms16, "value": pix_dm * args.steps * ws / f16["elapsed"],
                         "speedup_vs_fp32": ms_step / ms16,
-                        "roofline": path_roofline(sp16, "fp16", f16["delays"], ms16, hbm_peak, peak_src),
+                        "roofline": path_roofline(sp16, "fp16", f16["delays"], ms16, hbm_peak, peak_src,
+                                                  traffic16),
                         "kernel_ms_per_step": f16["per_push"], "candidates_per_step": f16["ncand"],
                         "host_ms_per_step": f16["host_ms"],
                         "clocks": clocks.summary(f16["t_wall0"], f16["t_wall1"])}
