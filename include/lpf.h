@@ -117,6 +117,20 @@ typedef struct {
      * sums (rows, then columns) of the stored band image.                        */
     int    kernel;        /* LPF_KERNEL_BOX / LPF_KERNEL_GAUSS                      default BOX */
     float  gauss_sigma;   /* s in pixels (> 0, finite) for LPF_KERNEL_GAUSS          default 0   */
+    /* Dispersed search only, opt-in: steady-source suppression.  The paper leaves
+     * steady sources to the stages after the search (association with the
+     * previous catalogue, Sec. 2.2; the network's DM estimate, Sec. 2.3).  With
+     * K = suppress_steady > 0 a pixel is steady once it has been a candidate of a
+     * trial whose delay row is all zero (no dispersion, t0 = T) in each of the K
+     * most recent pushes, and the candidates of every other trial at a steady
+     * pixel are dropped (the zero-delay trials keep theirs).  Persistence, not
+     * one frame: the last subband of a bright dispersed pulse can cross the
+     * threshold at zero delay in the frame it arrives, but not in K frames in a
+     * row for K above the pulse width.  The state (one byte per pixel) is updated
+     * by every push in order.  n_out of lpf_poll_candidates counts the kept
+     * candidates; when the list overflowed, the dropped ones are those among the
+     * stored records.  0 = off.                                                */
+    int    suppress_steady; /* 0..255                                             default 0   */
 } lpf_params;
 
 /* One candidate: pixel (y, x) of DM trial dm_idx (index into dm_grid) whose

@@ -28,6 +28,11 @@ method, each citing the passage of Ruhe et al. (arXiv 2103.15418) it follows:
   QCState, qc_frame  App. A, per-pixel running mean / standard deviation
                    (Welford) and scores zeta; bands over either threshold are
                    imputed with zeros
+  SteadyMask, suppress_steady  an opt-in reading of the steady-source removal
+                   the paper leaves to association (Sec. 2.2) and the network
+                   (Sec. 2.3): a pixel that was a candidate of a zero-delay trial
+                   in each of the K most recent pushes is steady, and the
+                   candidates of the other trials there are dropped
 
 Readings where the paper is silent or garbled (Sec. 2.1.1-2.1.2, Sec. 3.2, App. A):
   * C_DM = 4.148808e3 s MHz^2 cm^3 / pc (the printed unit "ms" is garbled; with
@@ -467,3 +472,36 @@ def clip_detect(D: np.ndarray, r: int, kappa: float, k: int = 1, iters: int = 1,
     q = local_max_mask(D, k)
     return dict(C=C, S=S, snr=snr, valid=S > 0, flags=flags, mask=flags & q & (S > 0),
                 lmax_margin=D - neighbour_max(D, k))
+
+
+# ---------------------------------------------------------------------------
+# Opt-in steady-source suppression.  The paper removes steady sources after the
+# search: association with the previous catalogue (Sec. 2.2) and the DM the
+# network infers (Sec. 2.3).  Reading: a steady source is bright without
+# dispersion in every frame, so a pixel counts as steady once it has been a
+# candidate of a zero-delay trial (max_f delay = 0, the newest frame alone) in
+# each of the K most recent pushes; a dispersed pulse can cross at zero delay in
+# the frame its last subband arrives, but not K frames in a row for K above its
+# width.  The candidates of every trial with a nonzero delay row at a steady
+# pixel are dropped; the zero-delay trials keep theirs.
+
+class SteadyMask:
+    """Run length, per pixel, of consecutive pushes in which the pixel was a
+    candidate of a zero-delay trial (saturating at 255)."""
+
+    def __init__(self, K: int):
+        self.K = int(K)
+        self.run: Dict[Tuple[int, int], int] = {}
+
+    def update(self, zero_delay_pixels) -> set:
+        """Fold in one push (the set of (y, x) of its zero-delay candidates) and
+        return the steady pixels after it (run >= K)."""
+        hit = set(zero_delay_pixels)
+        self.run = {p: min(self.run.get(p, 0) + 1, 255) for p in hit}
+        return {p for p, n in self.run.items() if n >= self.K}
+
+
+def suppress_steady(cands, max_delay_of_trial, steady: set):
+    """The candidates (t0, d, y, x, snr) without those of trials whose delay row
+    is not all zero at steady pixels."""
+    return [c for c in cands if max_delay_of_trial[c[1]] == 0 or (c[2], c[3]) not in steady]

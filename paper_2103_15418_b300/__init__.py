@@ -46,7 +46,8 @@ class Params(Structure):
                 ("dtype", c_int), ("cand_cap", c_int), ("dyn_box_r", c_int),
                 ("result_slots", c_int), ("cuda_stream", c_void_p), ("filter_impl", c_int),
                 ("qc", c_int), ("qc_z", c_float), ("qc_zeta", c_float), ("qc_min_frames", c_int),
-                ("mode", c_int), ("clip_iters", c_int), ("kernel", c_int), ("gauss_sigma", c_float)]
+                ("mode", c_int), ("clip_iters", c_int), ("kernel", c_int), ("gauss_sigma", c_float),
+                ("suppress_steady", c_int)]
 
 
 class Candidate(Structure):
@@ -178,7 +179,8 @@ def make_params(*, cadence_s: float = 1.0, kappa: float = 6.0, box_r: int = 15, 
                 cand_cap: int = 1 << 20, dyn_box_r: int = 0, result_slots: int = 2,
                 filter_impl: str = "auto", qc: bool = False, qc_z: float = 5.0, qc_zeta: float = 20.0,
                 qc_min_frames: int = 128, mode: str = "dispersed", lmax_r: int = 1,
-                clip_iters: int = 1, kernel: str = "box", gauss_sigma: float = 0.0) -> "Params":
+                clip_iters: int = 1, kernel: str = "box", gauss_sigma: float = 0.0,
+                suppress_steady: int = 0) -> "Params":
     p = default_params()
     p.cadence_s, p.kappa, p.box_r = cadence_s, kappa, box_r
     p.dtype, p.cand_cap, p.dyn_box_r, p.result_slots = DTYPES[dtype], cand_cap, dyn_box_r, result_slots
@@ -186,6 +188,7 @@ def make_params(*, cadence_s: float = 1.0, kappa: float = 6.0, box_r: int = 15, 
     p.qc, p.qc_z, p.qc_zeta, p.qc_min_frames = int(bool(qc)), qc_z, qc_zeta, qc_min_frames
     p.mode, p.lmax_r, p.clip_iters = MODES[mode], lmax_r, clip_iters
     p.kernel, p.gauss_sigma = KERNELS[kernel], gauss_sigma
+    p.suppress_steady = int(suppress_steady)
     return p
 
 
@@ -216,11 +219,13 @@ class Stream:
                  dyn_box_r: int = 0, result_slots: int = 2, cuda_stream=None,
                  filter_impl: str = "auto", qc: bool = False, qc_z: float = 5.0, qc_zeta: float = 20.0,
                  qc_min_frames: int = 128, mode: str = "dispersed", lmax_r: int = 1, clip_iters: int = 1,
-                 kernel: str = "box", gauss_sigma: float = 0.0):
+                 kernel: str = "box", gauss_sigma: float = 0.0, suppress_steady: int = 0):
         """mode "subband": the per-subband detector (dm_grid ignored, may be None; a
         candidate's dm_idx is its band, t0 its frame; lmax_r 3 gives the paper's 7x7
         maximum filter; kernel "gauss" with gauss_sigma s: the Gaussian background
-        kernel on the (2 box_r + 1)^2 window)."""
+        kernel on the (2 box_r + 1)^2 window).  suppress_steady K > 0: drop the
+        candidates of dispersed trials at pixels that were zero-delay candidates in
+        the K most recent pushes (lpf.h)."""
         lib = load()
         self.H, self.W = int(H), int(W)
         self.freqs = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
@@ -231,7 +236,8 @@ class Stream:
         p = make_params(cadence_s=cadence_s, kappa=kappa, box_r=box_r, dtype=dtype, cand_cap=cand_cap,
                         dyn_box_r=dyn_box_r, result_slots=result_slots, filter_impl=filter_impl, qc=qc,
                         qc_z=qc_z, qc_zeta=qc_zeta, qc_min_frames=qc_min_frames, mode=mode, lmax_r=lmax_r,
-                        clip_iters=clip_iters, kernel=kernel, gauss_sigma=gauss_sigma)
+                        clip_iters=clip_iters, kernel=kernel, gauss_sigma=gauss_sigma,
+                        suppress_steady=suppress_steady)
         if cuda_stream is not None:
             p.cuda_stream = int(getattr(cuda_stream, "cuda_stream", cuda_stream))
         self.params = p

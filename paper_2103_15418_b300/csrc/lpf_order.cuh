@@ -20,6 +20,7 @@
 namespace lpf {
 
 constexpr int kOrdThreads = 256;
+constexpr uint64_t kDropped = ~0ull;  // a record dropped by the steady-source mask (skipped below)
 constexpr int kOrdHist = 4096;      // ranks counted in shared memory (more: global atomics)
 constexpr int kOrdCap = 4096;       // bucket size sorted in shared memory
 
@@ -33,7 +34,9 @@ __global__ void __launch_bounds__(kOrdThreads) k_ord_count(const uint64_t* __res
     __syncthreads();
     const unsigned n = min(*n_ptr, (unsigned)cap);
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const unsigned r = (unsigned)(keys[i] >> shift);
+        const uint64_t key = keys[i];
+        if (key == kDropped) continue;
+        const unsigned r = (unsigned)(key >> shift);
         if (local) atomicAdd(&h[r], 1u);
         else atomicAdd(&counts[r], 1u);
     }
@@ -94,8 +97,8 @@ __global__ void __launch_bounds__(kOrdThreads) k_ord_scatter(const uint64_t* __r
     const unsigned stride = gridDim.x * blockDim.x;
     for (unsigned i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
         const unsigned i = i0 + threadIdx.x;
-        const bool valid = i < n;
-        const uint64_t key = valid ? kin[i] : 0ull;
+        const uint64_t key = i < n ? kin[i] : kDropped;
+        const bool valid = key != kDropped;
         const unsigned r = valid ? (unsigned)(key >> shift) : 0xffffffffu;
         const unsigned peers = __match_any_sync(0xffffffffu, r);
         const int leader = __ffs(peers) - 1;
@@ -189,5 +192,62 @@ __global__ void __launch_bounds__(kOrdThreads) k_ord_sort_format(
 }
 
 constexpr size_t ord_sort_smem_bytes() { return (size_t)kOrdCap * (sizeof(uint64_t) + sizeof(float)); }
+
+// ---------------------------------------------------------------------------
+// Opt-in steady-source suppression (between the 3x3 pass and the ordering; see
+// suppress_steady in lpf.h).  Pixels are indexed by the key's low bits (y << bx
+// | x), so the per-pixel state has 2^shift entries.
+//   k_steady_mark    bit of every pixel holding a candidate of a zero-delay
+//                    trial (max_f delay = 0) of this push
+//   k_steady_update  run[p] = bit ? min(run[p] + 1, 255) : 0: the pushes in a
+//                    row with such a candidate, in push order (tail stream)
+//   k_steady_apply   records of the other trials at pixels with run >= K get
+//                    the key kDropped (the ordering skips them); their number
+//                    is added to *dropped (one atomic per warp)
+__global__ void __launch_bounds__(kOrdThreads) k_steady_mark(const uint64_t* __restrict__ keys,
+                                                             const unsigned* __restrict__ n_ptr, int cap,
+                                                             int shift, const int* __restrict__ ord2d,
+                                                             const int* __restrict__ dmax_of_d,
+                                                             unsigned* __restrict__ bits) {
+    const unsigned n = min(*n_ptr, (unsigned)cap);
+    const uint64_t pm = (1ull << shift) - 1;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint64_t key = keys[i];
+        if (dmax_of_d[ord2d[key >> shift]] != 0) continue;
+        const uint64_t pix = key & pm;
+        atomicOr(&bits[pix >> 5], 1u << (pix & 31));
+    }
+}
+
+__global__ void __launch_bounds__(kOrdThreads) k_steady_update(const unsigned* __restrict__ bits,
+                                                               uint8_t* __restrict__ run, int64_t npix) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+        const bool hit = (bits[p >> 5] >> (p & 31)) & 1u;
+        const unsigned r = run[p];
+        run[p] = hit ? (uint8_t)min(r + 1u, 255u) : (uint8_t)0;
+    }
+}
+
+__global__ void __launch_bounds__(kOrdThreads) k_steady_apply(uint64_t* __restrict__ keys,
+                                                              const unsigned* __restrict__ n_ptr, int cap,
+                                                              int shift, const int* __restrict__ ord2d,
+                                                              const int* __restrict__ dmax_of_d,
+                                                              const uint8_t* __restrict__ run, int K,
+                                                              unsigned* __restrict__ dropped) {
+    const unsigned n = min(*n_ptr, (unsigned)cap);
+    const uint64_t pm = (1ull << shift) - 1;
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+        const unsigned i = i0 + threadIdx.x;
+        bool drop = false;
+        if (i < n) {
+            const uint64_t key = keys[i];
+            drop = dmax_of_d[ord2d[key >> shift]] != 0 && run[key & pm] >= K;
+            if (drop) keys[i] = kDropped;
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, drop);
+        if ((threadIdx.x & 31) == 0 && b) atomicAdd(dropped, (unsigned)__popc(b));
+    }
+}
 
 }  // namespace lpf

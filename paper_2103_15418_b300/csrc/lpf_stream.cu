@@ -57,7 +57,7 @@ int ceil_log2(int64_t v) {
 struct PushLane {
     uint64_t* keys[2] = {nullptr, nullptr};
     float* vals[2] = {nullptr, nullptr};
-    unsigned* counter = nullptr;       // [4]: candidates, -, crossings (u64 at word 2)
+    unsigned* counter = nullptr;       // [4]: candidates, dropped by the steady mask, crossings (u64 at word 2)
     uint64_t* xkeys = nullptr;         // threshold crossings of the residual path (row, y, x) ...
     float* xvals = nullptr;            // ... and their S/N
     unsigned* ord = nullptr;           // [3][n ranks]: records per trial rank, bucket starts, cursors
@@ -127,8 +127,12 @@ struct lpf_stream {
     cudaEvent_t yx_copied = nullptr; // the last staging copy has been read
     size_t device_bytes = 0;
 
+    // opt-in steady-source suppression (suppress_steady > 0): per pixel of the key
+    // space (2^(bx + by)), this push's zero-delay candidates and the run length
+    unsigned* steady_bits = nullptr; // [2^(bx+by) / 32]
+    uint8_t* steady_run = nullptr;   // [2^(bx+by)]
     // host pinned
-    unsigned* h_count = nullptr;     // [slots]
+    unsigned* h_count = nullptr;     // [slots][2]: records emitted, records dropped by the steady mask
     // quality control (App. A), when prm.qc: running per-pixel statistics of the
     // kept band images and the scratch of the three QC launches
     float* qc_mean = nullptr;        // [F][P]
@@ -232,6 +236,8 @@ void free_all(lpf_stream* s) {
     for (auto& e : s->lmax_ev)
         if (e) cudaEventDestroy(e);
     if (s->h_count) cudaFreeHost(s->h_count);
+    if (s->steady_bits) cudaFree(s->steady_bits);
+    if (s->steady_run) cudaFree(s->steady_run);
     if (s->h_yx) cudaFreeHost(s->h_yx);
     if (s->yx_copied) cudaEventDestroy(s->yx_copied);
     if (s->h_qc) cudaFreeHost(s->h_qc);
@@ -702,7 +708,7 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
     // the lane's crossing list, counters, candidate buffers and partials were last
     // used by the tail of the push two back
     LPF_TRY(cudaStreamWaitEvent(fs, L.tail_done, 0));
-    lpf::k_zero_u32<<<1, 32, 0, fs>>>(L.counter, 4);   // candidates, crossings (u64 at word 2)
+    lpf::k_zero_u32<<<1, 32, 0, fs>>>(L.counter, 4);   // candidates, dropped, crossings (u64 at word 2)
     prof_begin(s, sl, ST_FILTER, fs);
     lpf::FilterArgs a;
     if (n_rows > 0) {
@@ -746,6 +752,19 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
     }
     prof_end(s, sl, ST_LMAX, ts);
     LPF_TRY(cudaEventRecord(s->lmax_ev[seq % kLmaxEv], ts));
+    // opt-in steady-source suppression, in push order on the tail stream
+    if (s->prm.suppress_steady > 0) {
+        const int shift = s->bx + s->by;
+        const int64_t npix = (int64_t)1 << shift;
+        LPF_TRY(cudaMemsetAsync(s->steady_bits, 0, (size_t)(npix + 31) / 32 * sizeof(unsigned), ts));
+        lpf::k_steady_mark<<<kSortBlocks, lpf::kOrdThreads, 0, ts>>>(L.keys[0], L.counter, s->prm.cand_cap, shift,
+                                                                     s->d_ord2d, s->d_dmax, s->steady_bits);
+        lpf::k_steady_update<<<(unsigned)std::min<int64_t>((npix + 255) / 256, 148 * 16), 256, 0, ts>>>(
+            s->steady_bits, s->steady_run, npix);
+        lpf::k_steady_apply<<<kSortBlocks, lpf::kOrdThreads, 0, ts>>>(L.keys[0], L.counter, s->prm.cand_cap, shift,
+                                                                      s->d_ord2d, s->d_dmax, s->steady_run,
+                                                                      s->prm.suppress_steady, L.counter + 1);
+    }
     // ordering: counting sort on the trial rank, then each rank's bucket sorted by
     // pixel and formatted (lpf_order.cuh)
     {
@@ -771,7 +790,7 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
         lpf::k_stats<<<n_rows, 256, 0, ts>>>(L.partials, n_filter_blocks(s), slot.d_stats);
     prof_end(s, sl, ST_STATS, ts);
     if (cudaGetLastError() != cudaSuccess) return LPF_E_CUDA;
-    LPF_TRY(cudaMemcpyAsync(s->h_count + sl, L.counter, sizeof(unsigned), cudaMemcpyDeviceToHost, ts));
+    LPF_TRY(cudaMemcpyAsync(s->h_count + 2 * sl, L.counter, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, ts));
     if (s->prm.qc)
         LPF_TRY(cudaMemcpyAsync(s->h_qc + sl, slot.d_qc, sizeof(lpf::QcRecord), cudaMemcpyDeviceToHost, ts));
     if (n_rows > 0)
@@ -825,6 +844,7 @@ void lpf_default_params(lpf_params* p) {
     p->clip_iters = 1;
     p->kernel = LPF_KERNEL_BOX;
     p->gauss_sigma = 0.f;
+    p->suppress_steady = 0;
 }
 
 const char* lpf_strerror(int code) {
@@ -869,6 +889,7 @@ int plan_stream(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, 
     if (prm.kernel != LPF_KERNEL_BOX && prm.kernel != LPF_KERNEL_GAUSS) return LPF_E_ARG;
     const bool gauss = prm.kernel == LPF_KERNEL_GAUSS;
     if (gauss && (!band || !(prm.gauss_sigma > 0) || !std::isfinite(prm.gauss_sigma))) return LPF_E_ARG;
+    if (prm.suppress_steady < 0 || prm.suppress_steady > 255 || (prm.suppress_steady > 0 && band)) return LPF_E_ARG;
     // the per-subband detector with the box runs on the residual planes: streaming filter only
     if (band && !gauss && (prm.filter_impl == 1 || (prm.box_r != 7 && prm.box_r != 15))) return LPF_E_ARG;
     // iterated clipping: the per-subband detector, or the dispersed search on the
@@ -972,6 +993,10 @@ size_t footprint_bytes(const lpf_stream* s) {
     t += 2 * (2 * (b(cap * 8) + b(cap * 4)) + b(16) + b((size_t)3 * s->n_dm * 4) +
               b(nd * n_filter_blocks(s) * 3 * 8));
     t += (size_t)s->n_slots * (b(cap * sizeof(lpf::CandidateRec)) + b(nd * 3 * 8));
+    if (s->prm.suppress_steady > 0) {
+        const size_t npix = (size_t)1 << (s->bx + s->by);
+        t += b(npix / 8) + b(npix);
+    }
     return t;
 }
 
@@ -1074,6 +1099,13 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
                              cudaEventCreateWithFlags(&L.tail_done, cudaEventDisableTiming) != cudaSuccess))
             rc = LPF_E_CUDA;
     }
+    if (rc == LPF_OK && prm.suppress_steady > 0) {
+        const size_t npix = (size_t)1 << (s->bx + s->by);
+        rc = dev_alloc(s, &s->steady_bits, std::max<size_t>(npix / 32, 1));
+        if (rc == LPF_OK) rc = dev_alloc(s, &s->steady_run, npix);
+        // no pixel has a run yet
+        if (rc == LPF_OK && cudaMemsetAsync(s->steady_run, 0, npix, s->st) != cudaSuccess) rc = LPF_E_CUDA;
+    }
     for (int i = 0; i < s->n_slots && rc == LPF_OK; ++i) {
         rc = dev_alloc(s, &s->slots[i].d_out, (size_t)prm.cand_cap);
         if (rc == LPF_OK) rc = dev_alloc(s, &s->slots[i].d_stats, (size_t)s->n_distinct * 3);
@@ -1117,7 +1149,7 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
             for (int e = 0; e < 2 && rc == LPF_OK; ++e)
                 if (cudaEventCreate(&s->ev[k][i][e]) != cudaSuccess) rc = LPF_E_CUDA;
     if (rc == LPF_OK) {
-        if (cudaMallocHost(&s->h_count, sizeof(unsigned) * kMaxSlots) != cudaSuccess ||
+        if (cudaMallocHost(&s->h_count, 2 * sizeof(unsigned) * kMaxSlots) != cudaSuccess ||
             cudaMallocHost(&s->h_stats, sizeof(double) * kMaxSlots * s->n_distinct * 3) != cudaSuccess) {
             cudaGetLastError();
             rc = LPF_E_OOM;
@@ -1206,8 +1238,11 @@ int lpf_poll_candidates(lpf_stream* s, lpf_candidate* out_host, int cap, int* n_
         s->last_qc = s->h_qc[sl];
         s->last_qc_T = slot.T;
     }
-    const unsigned found = s->h_count[sl];
-    const unsigned stored = std::min<unsigned>(found, (unsigned)s->prm.cand_cap);
+    // records emitted (may exceed the list), and those the steady mask dropped
+    // (among the stored ones)
+    const unsigned emitted = s->h_count[2 * sl], dropped = s->h_count[2 * sl + 1];
+    const unsigned found = emitted - dropped;
+    const unsigned stored = std::min<unsigned>(emitted, (unsigned)s->prm.cand_cap) - dropped;
     const unsigned ncopy = std::min<unsigned>(stored, (unsigned)cap);
     if (ncopy > 0) {
         LPF_TRY(cudaMemcpyAsync(out_host, slot.d_out, (size_t)ncopy * sizeof(lpf_candidate),
@@ -1233,7 +1268,7 @@ int lpf_poll_candidates(lpf_stream* s, lpf_candidate* out_host, int cap, int* n_
     s->polled_T = slot.T;
     s->polled_slot = sl;
     s->pending.pop_front();
-    if (found > (unsigned)s->prm.cand_cap || found > (unsigned)cap) return LPF_E_TRUNCATED;
+    if (emitted > (unsigned)s->prm.cand_cap || found > (unsigned)cap) return LPF_E_TRUNCATED;
     return LPF_OK;
 }
 

@@ -239,3 +239,22 @@ def test_cnn_arguments_are_checked_before_any_cuda_call():
         assert e.value.code == lpf.LPF_E_ARG, (F, Tw, mb)
     with pytest.raises(ValueError):
         lpf.Cnn(8, 16, p[:-1], max_batch=4)
+
+
+def test_steady_suppression_arguments_and_footprint():
+    """suppress_steady: 0..255, dispersed search only; its state is one bit and one
+    byte per pixel of the 2^(bx + by) key space, planned without a GPU."""
+    import synth
+    lib = lpf
+    spec = synth.spec_tiny()
+    fp = lambda **kw: lib.footprint(spec.H, spec.W, spec.freqs_mhz, spec.dm_grid, spec.depth,
+                                    box_r=spec.box_r, **kw)
+    npix = 1 << (2 * int(np.ceil(np.log2(spec.W))))          # 64 x 64: 6 + 6 key bits
+    assert spec.H == spec.W == 64
+    assert fp(suppress_steady=3) - fp() == npix // 8 + npix
+    assert fp(suppress_steady=255) == fp(suppress_steady=1)
+    for bad in (-1, 256):
+        with pytest.raises(lib.LpfError):
+            fp(suppress_steady=bad)
+    with pytest.raises(lib.LpfError):
+        lib.footprint(spec.H, spec.W, spec.freqs_mhz, None, 1, box_r=7, mode="subband", suppress_steady=2)

@@ -794,3 +794,53 @@ def test_pins_catch_planted_clip_mistakes():
         C = O.box_sum(D * m, r) / n
         return C, O.box_sum((D - C) ** 2 * m, r) / n
     assert not _clip_pin_holds(full_count)
+
+
+# ---------------------------------------------------------------------------
+# opt-in steady-source suppression (a reading of Sec. 2.2 / 2.3 removal)
+
+def test_steady_mask_needs_k_pushes_in_a_row():
+    m = O.SteadyMask(3)
+    a, b = (5, 7), (9, 1)
+    seq = [{a}, {a, b}, {a, b}, {b}, {a, b}, {a, b}, {a}]
+    got = [m.update(s) for s in seq]
+    # a: runs 1, 2, 3, 0, 1, 2, 3 -> steady at the third and the seventh push
+    # b: runs 0, 1, 2, 3, 4, 5, 0 -> steady at the fourth to the sixth push
+    assert got == [set(), set(), {a}, {b}, {b}, {b}, {a}]
+
+
+def test_suppress_steady_drops_only_dispersed_trials_at_steady_pixels():
+    dmax = np.array([0, 0, 3, 5])                    # trials 0 and 1: zero delay rows
+    cands = [(10, 0, 5, 5, 9.0), (10, 1, 5, 5, 9.0), (7, 2, 5, 5, 8.0), (5, 3, 5, 5, 7.0),
+             (7, 2, 6, 6, 8.0), (5, 3, 1, 2, 7.0)]
+    kept = O.suppress_steady(cands, dmax, {(5, 5)})
+    assert kept == [(10, 0, 5, 5, 9.0), (10, 1, 5, 5, 9.0), (7, 2, 6, 6, 8.0), (5, 3, 1, 2, 7.0)]
+    assert O.suppress_steady(cands, dmax, set()) == cands
+
+
+def test_steady_sources_suppressed_and_pulse_kept_on_a_stream():
+    """On the tiny stream (three steady 20-sigma sources, one pulse at DM 7,
+    kappa 4): once the sources have been zero-delay candidates K pushes in a row,
+    no dispersed trial keeps a candidate at a source pixel, and the pulse's
+    candidates are untouched."""
+    spec = synth.spec_tiny(kappa=4.0)
+    st = synth.SyntheticStream(spec, seed=3)
+    delays = O.delay_table(spec.freqs_mhz, spec.dm_grid, spec.cadence_s)
+    dmax = delays.max(axis=1)
+    assert (dmax == 0).any() and (dmax > 0).any()
+    src = {(y, x) for y, x, _ in st.sources}
+    frame_at = lambda t: st.frame(t).astype(np.float64)
+    K = 3
+    mask = O.SteadyMask(K)
+    dropped_at_sources = 0
+    for T in range(20):
+        cands, _, _ = O.search_push(frame_at, T, delays, spec.box_r, spec.kappa)
+        steady = mask.update({(c[2], c[3]) for c in cands if dmax[c[1]] == 0})
+        kept = O.suppress_steady(cands, dmax, steady)
+        if T >= K - 1:
+            assert src <= steady, (T, src - steady)
+            assert not [c for c in kept if dmax[c[1]] > 0 and (c[2], c[3]) in src]
+        dropped_at_sources += sum(1 for c in cands if dmax[c[1]] > 0 and (c[2], c[3]) in src)
+        # nothing outside the steady pixels is dropped
+        assert [c for c in cands if (c[2], c[3]) not in steady] == [c for c in kept if (c[2], c[3]) not in steady]
+    assert dropped_at_sources > 0
