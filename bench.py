@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--gauss-sigma", type=float, default=0.0,
                     help="subband workload: Gaussian background kernel of this width in pixels on the "
                          "31x31 window (0 = the uniform box)")
+    ap.add_argument("--suppress-steady", type=int, default=0,
+                    help="steady-source suppression: K pushes in a row at zero delay (0 = off)")
     ap.add_argument("--qc", action="store_true",
                     help="quality control of every frame before the search (band and pixel scores)")
     ap.add_argument("--workload", default="aartfaac", choices=["aartfaac", "serving", "subband", "stress"],
@@ -335,7 +337,8 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
-def measure(lpf, torch, dev, spec, dtype, steps, warmup, pool_n, seed, qc=False, e2e_steps=0, dist=None):
+def measure(lpf, torch, dev, spec, dtype, steps, warmup, pool_n, seed, qc=False, e2e_steps=0, dist=None,
+            suppress_steady=0):
     """Device-timed steps of one stream (and, with e2e_steps, the end-to-end loop with
     host buffers).  The ring is filled first, so every trial is active."""
     st = synth.SyntheticStream(spec, seed=seed)
@@ -345,7 +348,7 @@ def measure(lpf, torch, dev, spec, dtype, steps, warmup, pool_n, seed, qc=False,
     cur = torch.cuda.Stream(dev)            # the search stream (the timing events are recorded on it)
     s = lpf.Stream(spec.H, spec.W, spec.freqs_mhz, spec.dm_grid, spec.depth, kappa=spec.kappa,
                    box_r=spec.box_r, dtype=dtype, result_slots=RESULT_SLOTS, cuda_stream=cur,
-                   qc=qc, qc_min_frames=16)
+                   qc=qc, qc_min_frames=16, suppress_steady=suppress_steady)
     out = {"info": s.info(), "delays": s.delay_table()}
     T = 0
     polled = []
@@ -461,7 +464,7 @@ def run_ours(args):
     clocks.start()                     # before the ring fill, so the short timed region has samples
     spec = workload_spec(args.dtype)
     m = measure(lpf, torch, dev, spec, args.dtype, args.steps, args.warmup, args.pool, 1 + rank, qc=args.qc,
-                e2e_steps=args.e2e_steps, dist=dist)
+                e2e_steps=args.e2e_steps, dist=dist, suppress_steady=args.suppress_steady)
     f16 = None
     if not args.no_fp16 and args.dtype == "fp32" and not args.qc:
         f16 = measure(lpf, torch, dev, workload_spec("fp16"), "fp16", args.steps, args.warmup, args.pool,
@@ -548,9 +551,10 @@ def run_ours(args):
                    "dm_trials": spec.n_dm, "depth": spec.depth, "box": 2 * spec.box_r + 1,
                    "storage": args.dtype, "arithmetic": "f32 (delay table f64, statistics f64)",
                    "distinct_delay_rows": nd, "quality_control": bool(args.qc),
+                   "suppress_steady": args.suppress_steady,
                    "l2": "inputs larger than L2 (ring %.2f GB)" % (info["ring_bytes"] / 1e9),
                    "parallelism": f"{ws} independent stream(s), one per GPU"},
-        "gpu_launches": int(args.steps * launches_per_push(spec, args.qc)),
+        "gpu_launches": int(args.steps * launches_per_push(spec, args.qc, args.suppress_steady)),
         "roofline": roof,
         "rooflines": rooflines,
         "kernel_ms_per_step": per_push,
@@ -616,11 +620,12 @@ def cnn_throughput(lpf, torch, n=10000, F=32, Tw=64, steps=20, warmup=3):
             "flop_per_batch": flops}
 
 
-def launches_per_push(spec, qc):
+def launches_per_push(spec, qc, suppress_steady=0):
     """Kernels of one push: residuals, counter reset, shift-sum, ring write, filter,
     3x3 pass, 4 ordering kernels (count, scan, scatter, sort + format), statistics
-    (+ 2 with quality control)."""
-    return 11 + (2 if qc else 0)
+    (+ 2 with quality control, + 3 with steady-source suppression: mark, update,
+    apply)."""
+    return 11 + (2 if qc else 0) + (3 if suppress_steady else 0)
 
 
 # ---------------------------------------------------------------------------
