@@ -67,7 +67,9 @@ __global__ void __launch_bounds__(256) k_dedisperse(
                 a0 = __fadd2_rn(a0, make_float2(cur[f].x, cur[f].y));
                 a1 = __fadd2_rn(a1, make_float2(cur[f].z, cur[f].w));
             }
-        *reinterpret_cast<float4*>(dst) = make_float4(a0.x, a0.y, a1.x, a1.y);
+        // streaming stores: the 0.84 GB of R images should not push ring planes that
+        // later rows reload out of L2
+        __stcs(reinterpret_cast<float4*>(dst), make_float4(a0.x, a0.y, a1.x, a1.y));
         dst += P;
     }
 }
@@ -128,8 +130,8 @@ __global__ void __launch_bounds__(256) k_dedisperse16(
                 for (int k = 0; k < 4; ++k) add_pair((&cur[f].x)[k], a[k].x, a[k].y, static_cast<const TS*>(nullptr));
             }
         float4* o = reinterpret_cast<float4*>(dst);
-        o[0] = make_float4(a[0].x, a[0].y, a[1].x, a[1].y);
-        o[1] = make_float4(a[2].x, a[2].y, a[3].x, a[3].y);
+        __stcs(o, make_float4(a[0].x, a[0].y, a[1].x, a[1].y));          // streaming, as above
+        __stcs(o + 1, make_float4(a[2].x, a[2].y, a[3].x, a[3].y));
         dst += P;
     }
 }
