@@ -8,7 +8,7 @@ tolerances.  Report: S/N error and candidate-set symmetric difference against
 the oracle on the unrounded frames, asserted within the same tolerances and
 zero.  Workloads: the 2048^2 precision stream (AARTFAAC bands, 501 trials, DM
 step 0.5, depth 48, 40 pulses) in FP32, FP16 and BF16; the 1024^2 AARTFAAC
-stream in FP16.  The oracle runs on sampled trials of one push.
+stream in FP16 and BF16.  The oracle runs on sampled trials of one push.
 """
 import json
 
@@ -110,10 +110,10 @@ def test_precision_report_2048(lib, capsys):
     assert rep["fp16"]["max_rel_snr_err"] <= 2e-3
 
 
-def test_precision_report_aartfaac_fp16(lib, capsys):
+def test_precision_report_aartfaac_16bit(lib, capsys):
     spec = synth.spec_aartfaac(n_frames=60)
     dms = [0, 1, 37, 100, 173, 250]
-    T, delays, planes, res = run_storage_types(lib, spec, 2, dms, ("fp16",))
+    T, delays, planes, res = run_storage_types(lib, spec, 2, dms, ("fp16", "bf16"))
     rep = report_for(spec, T, delays, planes, res, dms)
     with capsys.disabled():
         print("\nPRECISION_REPORT " + json.dumps({"aartfaac-1024x1024-16sb-251dm-depth48": rep}))
