@@ -469,13 +469,13 @@ int set_res_attributes() {
 }
 
 // Shift-sum of a ring (raw: D; residual: R = D - C) into out; the rows are
-// split into two segments (each restarts its register state) for parallelism.
+// split into segments (each restarts its register state) for parallelism.
 template <typename TS>
 void launch_dedisperse_ring(lpf_stream* s, const void* ring_v, float* out, int n_rows, int Tmod) {
-    // two row segments for FP32 rings, three for 16-bit rings (whose threads own 8
-    // pixels, so half as many CTAs per segment); more where one segment's plane
-    // table would exceed 48 KB of shared memory
-    int nseg = n_rows >= 32 ? (sizeof(TS) == 4 ? 2 : 3) : 1;
+    // three row segments for FP32 rings, four for 16-bit rings (whose threads own 8
+    // pixels, so half as many CTAs per segment; measured against 1-2 and 4-5);
+    // more where one segment's plane table would exceed 48 KB of shared memory
+    int nseg = n_rows >= 32 ? (sizeof(TS) == 4 ? 3 : 4) : 1;
     while (lpf::dedisperse_smem_bytes((n_rows + nseg - 1) / nseg, s->F) > 48 * 1024) ++nseg;
     const int seg = (n_rows + nseg - 1) / nseg;
     const size_t smem = lpf::dedisperse_smem_bytes(seg, s->F);
