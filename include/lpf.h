@@ -213,7 +213,9 @@ int lpf_push_frame_host(lpf_stream* s, const float* frame_host, int64_t T);
  * the first min(cap, cand_cap) records of the found set, sorted; which records
  * were dropped beyond cand_cap is unspecified) when *n_out > cap or the device
  * capacity cand_cap overflowed; LPF_E_TIMEOUT (frame stays queued) or
- * LPF_E_NODATA otherwise.  out_host may be NULL when cap == 0.
+ * LPF_E_NODATA otherwise.  out_host may be NULL when cap == 0.  With
+ * suppress_steady, *n_out and the records exclude the dropped candidates (see
+ * lpf_params).
  */
 int lpf_poll_candidates(lpf_stream* s, lpf_candidate* out_host, int cap, int* n_out,
                         int64_t* T_out, int timeout_ms);
