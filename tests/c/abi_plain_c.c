@@ -23,8 +23,13 @@ int main(void) {
     lpf_params bad = p;
     bad.box_r = 17;
     int rc_arg = lpf_stream_footprint(1024, 1024, 16, freqs, 251, dms, 48, &bad, &unused);
+    lpf_params sup = p;
+    sup.suppress_steady = 8;
+    size_t bytes_sup = 0;
+    int rc_sup = lpf_stream_footprint(1024, 1024, 16, freqs, 251, dms, 48, &sup, &bytes_sup);
     const char* name = lpf_strerror(LPF_E_DEPTH);
-    printf("%d %zu %d %zu %d %d %d %d %.1f %s\n", rc, bytes, rc_null, bytes_null, rc_depth, rc_arg, p.box_r,
-           p.cand_cap, (double)p.kappa, strlen(name) > 0 ? "named" : "unnamed");
+    printf("%d %zu %d %zu %d %d %d %d %.1f %s %d %zu %zu\n", rc, bytes, rc_null, bytes_null, rc_depth, rc_arg,
+           p.box_r, p.cand_cap, (double)p.kappa, strlen(name) > 0 ? "named" : "unnamed", rc_sup, bytes_sup,
+           sizeof(lpf_params));
     return 0;
 }

@@ -40,6 +40,13 @@ def test_struct_layouts():
     assert (p.filter_impl, p.qc, p.qc_z, p.qc_zeta, p.qc_min_frames, p.mode, p.clip_iters) == \
         (0, 0, 5.0, 20.0, 128, 0, 1)
     assert (p.kernel, p.gauss_sigma) == (0, 0.0)
+    # the last field: the library's defaults overwrite a sentinel at the binding's
+    # offset of it, and the struct sizes agree
+    q = lpf.Params()
+    q.suppress_steady = 77
+    lpf.load().lpf_default_params(ctypes.byref(q))
+    assert q.suppress_steady == 0
+    assert lpf.Params.suppress_steady.offset + 4 <= ctypes.sizeof(lpf.Params)
 
 
 def test_strerror_names_every_code():

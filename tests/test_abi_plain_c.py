@@ -1,6 +1,7 @@
 """The C ABI from plain C: tests/c/abi_plain_c.c includes include/lpf.h as C99
 (no C++), links liblpf.so and calls the entry points that need no GPU; its
 results must equal the same calls made through the Python binding."""
+import ctypes
 import os
 import shutil
 import subprocess
@@ -36,3 +37,7 @@ def test_header_compiles_as_c99_and_calls_agree():
     assert int(out[4]) == lpf.LPF_E_DEPTH and int(out[5]) == lpf.LPF_E_ARG
     assert (int(out[6]), int(out[7]), float(out[8])) == (15, 1 << 20, 6.0)
     assert out[9] == "named" and lib.lpf_strerror(lpf.LPF_E_DEPTH)
+    # the last field of lpf_params set from C: the same plan as through the binding
+    assert int(out[10]) == lpf.LPF_OK
+    assert int(out[11]) == lpf.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth, suppress_steady=8) > want
+    assert int(out[12]) == ctypes.sizeof(lpf.Params)
