@@ -128,8 +128,10 @@ typedef struct {
      * threshold at zero delay in the frame it arrives, but not in K frames in a
      * row for K above the pulse width.  The state (one byte per pixel) is updated
      * by every push in order.  n_out of lpf_poll_candidates counts the kept
-     * candidates; when the list overflowed, the dropped ones are those among the
-     * stored records.  0 = off.                                                */
+     * candidates.  When the list overflowed (cand_cap records stored) the mask
+     * is applied to the stored records only, the total is not known, and n_out
+     * is the number of kept records among the stored ones (the poll returns
+     * LPF_E_TRUNCATED).  0 = off.                                              */
     int    suppress_steady; /* 0..255                                             default 0   */
 } lpf_params;
 
@@ -210,12 +212,14 @@ int lpf_push_frame_host(lpf_stream* s, const float* frame_host, int64_t T);
  * forever) for its work, then copies its candidates into out_host[cap] (HOST),
  * sorted by (t0, dm_idx, y, x), and sets *n_out to the total number found and
  * *T_out to the frame index.  Returns LPF_E_TRUNCATED (with out_host holding
- * the first min(cap, cand_cap) records of the found set, sorted; which records
+ * min(cap, cand_cap, *n_out) records of the found set, sorted; which records
  * were dropped beyond cand_cap is unspecified) when *n_out > cap or the device
  * capacity cand_cap overflowed; LPF_E_TIMEOUT (frame stays queued) or
  * LPF_E_NODATA otherwise.  out_host may be NULL when cap == 0.  With
- * suppress_steady, *n_out and the records exclude the dropped candidates (see
- * lpf_params).
+ * suppress_steady, *n_out and the records exclude the dropped candidates, and
+ * after an overflow of cand_cap *n_out is the number of kept records stored
+ * (see lpf_params).  In every case out_host holds min(cap, cand_cap, *n_out)
+ * records.
  */
 int lpf_poll_candidates(lpf_stream* s, lpf_candidate* out_host, int cap, int* n_out,
                         int64_t* T_out, int timeout_ms);

@@ -1239,10 +1239,14 @@ int lpf_poll_candidates(lpf_stream* s, lpf_candidate* out_host, int cap, int* n_
         s->last_qc_T = slot.T;
     }
     // records emitted (may exceed the list), and those the steady mask dropped
-    // (among the stored ones)
+    // (among the stored ones); the stored records left are the ones formatted.
+    // Without the mask the total found is the emitted count.  With it, records
+    // past cand_cap were never checked against the mask, so the total of kept
+    // candidates is known only without overflow; with overflow it is reported as
+    // the kept records stored, so that out_host always holds min(cap, found).
     const unsigned emitted = s->h_count[2 * sl], dropped = s->h_count[2 * sl + 1];
-    const unsigned found = emitted - dropped;
     const unsigned stored = std::min<unsigned>(emitted, (unsigned)s->prm.cand_cap) - dropped;
+    const unsigned found = s->prm.suppress_steady > 0 ? stored : emitted;
     const unsigned ncopy = std::min<unsigned>(stored, (unsigned)cap);
     if (ncopy > 0) {
         LPF_TRY(cudaMemcpyAsync(out_host, slot.d_out, (size_t)ncopy * sizeof(lpf_candidate),

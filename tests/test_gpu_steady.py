@@ -70,3 +70,55 @@ def test_steady_suppression_against_the_oracle(lib, dtype):
                 abs(maps[d]["snr"][p] - spec.kappa) < band for p in ora_steady ^ steady for d in np.flatnonzero(dmax == 0)
             ), (T, ora_steady ^ steady)
     assert dropped_total > 0
+
+
+def test_steady_suppression_on_the_tiled_path_and_with_a_full_list(lib):
+    """The same drop rule on the tiled filter path (records emitted by the filter
+    itself), and with a candidate list too small for a push: truncation is
+    reported, n_out is the number of records returned (the records past the list
+    were never checked against the mask), they are sorted, and the drop rule
+    holds for the marks the device saw (its stored zero-delay records)."""
+    spec = synth.spec_tiny(kappa=4.0)
+    st = synth.SyntheticStream(spec, seed=3)
+    delays = O.delay_table(spec.freqs_mhz, spec.dm_grid, spec.cadence_s)
+    dmax = delays.max(axis=1)
+    K = 2
+    mask, mask_s = O.SteadyMask(K), O.SteadyMask(K)
+    kw = dict(kappa=spec.kappa, box_r=spec.box_r)
+    saw_trunc = saw_drop = False
+    with lib.Stream(spec.H, spec.W, spec.freqs_mhz, spec.dm_grid, spec.depth, **kw) as full, \
+         lib.Stream(spec.H, spec.W, spec.freqs_mhz, spec.dm_grid, spec.depth, suppress_steady=K,
+                    filter_impl="tiled", **kw) as tiled, \
+         lib.Stream(spec.H, spec.W, spec.freqs_mhz, spec.dm_grid, spec.depth, suppress_steady=K,
+                    cand_cap=24, **kw) as small:
+        for T in range(16):
+            x = torch.from_numpy(st.frame(T)).cuda()
+            for s in (full, tiled, small):
+                s.push(x, T)
+            _, c0, n0, _ = full.poll(timeout_ms=60000)
+            _, ct, nt, trunc_t = tiled.poll(timeout_ms=60000)
+            _, cs, ns, trunc_s = small.poll(timeout_ms=60000)
+            all0 = {(int(r["t0"]), int(r["dm_idx"]), int(r["y"]), int(r["x"])) for r in c0}
+            steady = mask.update({(k[2], k[3]) for k in all0 if dmax[k[1]] == 0})
+            want = {r[:4] for r in O.suppress_steady([k + (0.0,) for k in all0], dmax, steady)}
+            got_t = {(int(r["t0"]), int(r["dm_idx"]), int(r["y"]), int(r["x"])) for r in ct}
+            # the tiled filter computes the same S/N within FP32 rounding: the sets
+            # agree (the tiny stream has no pixel within 1e-3 of kappa here)
+            assert not trunc_t and nt == len(ct) and got_t == want, (T, got_t ^ want)
+            got_s = [(int(r["t0"]), int(r["dm_idx"]), int(r["y"]), int(r["x"])) for r in cs]
+            assert_sorted_unique(cs)
+            assert set(got_s) <= all0 and len(got_s) == min(ns, 24)
+            # zero-delay records are never dropped, so the returned ones are the
+            # marks the device saw: replay the oracle mask on them
+            steady_s = mask_s.update({(k[2], k[3]) for k in got_s if dmax[k[1]] == 0})
+            assert not [k for k in got_s if dmax[k[1]] > 0 and (k[2], k[3]) in steady_s], T
+            if n0 > 24:
+                # the list overflowed: the mask saw only the stored records, and
+                # n_out counts the kept ones among them (all returned)
+                assert trunc_s and ns == len(got_s)
+                saw_trunc = True
+                saw_drop |= ns < 24                         # a stored record was dropped
+            else:
+                kept = {r[:4] for r in O.suppress_steady([k + (0.0,) for k in all0], dmax, steady_s)}
+                assert not trunc_s and set(got_s) == kept and ns == len(kept), T
+    assert saw_trunc and saw_drop
