@@ -267,7 +267,7 @@ int lpf_extract_dynspec(lpf_stream* s, const lpf_candidate* c_host, int n, int T
  * returning), so nothing carries over between calls and the next call may
  * start as soon as this one returns.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress, with that
- * device current); make that first call before any stream capture.
+ * device current).
  */
 #define LPF_STATIC_DYNSPEC_MAX 65536
 int lpf_extract_dynspec_static(lpf_stream* s, const lpf_candidate* c_host, int n, int Tw,
