@@ -623,9 +623,10 @@ def cnn_throughput(lpf, torch, n=10000, F=32, Tw=64, steps=20, warmup=3):
 def launches_per_push(spec, qc, suppress_steady=0):
     """Kernels of one push: residuals, counter reset, shift-sum, ring write, filter,
     3x3 pass, 4 ordering kernels (count, scan, scatter, sort + format), statistics
-    (+ 2 with quality control, + 3 with steady-source suppression: mark, update,
-    apply)."""
-    return 11 + (2 if qc else 0) + (3 if suppress_steady else 0)
+    (+ 2 with quality control, + 2 with steady-source suppression: run-length
+    update and drop; the zero-delay marks are set by the kernels that find the
+    candidates, after a memset of the lane's bit map)."""
+    return 11 + (2 if qc else 0) + (2 if suppress_steady else 0)
 
 
 # ---------------------------------------------------------------------------

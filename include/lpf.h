@@ -127,11 +127,12 @@ typedef struct {
      * one frame: the last subband of a bright dispersed pulse can cross the
      * threshold at zero delay in the frame it arrives, but not in K frames in a
      * row for K above the pulse width.  The state (one byte per pixel) is updated
-     * by every push in order.  n_out of lpf_poll_candidates counts the kept
-     * candidates.  When the list overflowed (cand_cap records stored) the mask
-     * is applied to the stored records only, the total is not known, and n_out
-     * is the number of kept records among the stored ones (the poll returns
-     * LPF_E_TRUNCATED).  0 = off.                                              */
+     * by every push in order, from every zero-delay candidate the push finds
+     * (stored in the list or not), so it does not depend on cand_cap.  n_out of
+     * lpf_poll_candidates counts the kept candidates.  When the list overflowed
+     * (cand_cap records stored) the drop is applied to the stored records only,
+     * the total is not known, and n_out is the number of kept records among the
+     * stored ones (the poll returns LPF_E_TRUNCATED).  0 = off.               */
     int    suppress_steady; /* 0..255                                             default 0   */
 } lpf_params;
 

@@ -347,6 +347,7 @@ __global__ void __launch_bounds__(256) k_clip_emit(ClipArgs c, FilterArgs a, int
                 if (cand) {
                     const unsigned base = b0 + __popc(bal & ((1u << lane) - 1u)) * (unsigned)nm;
                     const uint64_t pix = ((uint64_t)y << a.bx) | (uint64_t)x;
+                    mark_zero_row(a, f, pix);
                     for (int m = 0; m < nm; ++m) {
                         const unsigned idx = base + (unsigned)m;
                         if (idx < (unsigned)a.cap) {

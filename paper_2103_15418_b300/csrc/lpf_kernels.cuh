@@ -160,7 +160,15 @@ struct FilterArgs {
     int cap;
     int bx, by;            // bits of x and y in the key
     double* partials;      // [n_rows][tiles][3]
+    unsigned* zbits = nullptr;  // steady-source marks (null: off): one bit per key pixel y << bx | x
+    int zrow = -1;              // the delay row that is all zero (no dispersion), -1 if none
 };
+
+// Steady-source marks: a candidate of the all-zero delay row sets its pixel's
+// bit as it is found, whether or not its records fit the candidate list.
+__device__ __forceinline__ void mark_zero_row(const FilterArgs& a, int row, uint64_t pix) {
+    if (a.zbits != nullptr && row == a.zrow) atomicOr(&a.zbits[pix >> 5], 1u << (pix & 31));
+}
 
 __device__ __forceinline__ int odd_stride(int n) { return n | 1; }
 
@@ -309,6 +317,7 @@ __global__ void __launch_bounds__(kFilterThreads, 1) k_filter(FilterArgs a) {
                     if (cand) {
                         unsigned rank = __popc(bal & ((1u << lane) - 1u));
                         uint64_t pix = ((uint64_t)y << a.bx) | (uint64_t)x;
+                        mark_zero_row(a, row, pix);
                         for (int m = 0; m < nm; ++m) {
                             unsigned idx = base + rank * nm + m;
                             if (idx < (unsigned)a.cap) {

@@ -196,35 +196,32 @@ constexpr size_t ord_sort_smem_bytes() { return (size_t)kOrdCap * (sizeof(uint64
 // ---------------------------------------------------------------------------
 // Opt-in steady-source suppression (between the 3x3 pass and the ordering; see
 // suppress_steady in lpf.h).  Pixels are indexed by the key's low bits (y << bx
-// | x), so the per-pixel state has 2^shift entries.
-//   k_steady_mark    bit of every pixel holding a candidate of a zero-delay
-//                    trial (max_f delay = 0) of this push
+// | x), so the per-pixel state has 2^shift entries.  The kernels that find the
+// candidates set the bit of every pixel with a candidate of the all-zero delay
+// row of the push (mark_zero_row), stored in the list or not; then
 //   k_steady_update  run[p] = bit ? min(run[p] + 1, 255) : 0: the pushes in a
-//                    row with such a candidate, in push order (tail stream)
+//                    row with such a candidate, in push order (tail stream);
+//                    each word of the bit map is cleared once its warp has read
+//                    it, ready for the lane's next push
 //   k_steady_apply   records of the other trials at pixels with run >= K get
 //                    the key kDropped (the ordering skips them); their number
 //                    is added to *dropped (one atomic per warp)
-__global__ void __launch_bounds__(kOrdThreads) k_steady_mark(const uint64_t* __restrict__ keys,
-                                                             const unsigned* __restrict__ n_ptr, int cap,
-                                                             int shift, const int* __restrict__ ord2d,
-                                                             const int* __restrict__ dmax_of_d,
-                                                             unsigned* __restrict__ bits) {
-    const unsigned n = min(*n_ptr, (unsigned)cap);
-    const uint64_t pm = (1ull << shift) - 1;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint64_t key = keys[i];
-        if (dmax_of_d[ord2d[key >> shift]] != 0) continue;
-        const uint64_t pix = key & pm;
-        atomicOr(&bits[pix >> 5], 1u << (pix & 31));
-    }
-}
-
-__global__ void __launch_bounds__(kOrdThreads) k_steady_update(const unsigned* __restrict__ bits,
+// The lanes of a warp take the 32 pixels of one word (blockDim and the grid
+// stride are multiples of 32, npix is a power of two).
+__global__ void __launch_bounds__(kOrdThreads) k_steady_update(unsigned* __restrict__ bits,
                                                                uint8_t* __restrict__ run, int64_t npix) {
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
-        const bool hit = (bits[p >> 5] >> (p & 31)) & 1u;
-        const unsigned r = run[p];
-        run[p] = hit ? (uint8_t)min(r + 1u, 255u) : (uint8_t)0;
+    for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x; p0 < npix; p0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = p0 + threadIdx.x;
+        const bool valid = p < npix;                          // false only when npix < 32
+        unsigned w = 0u;
+        if (valid) {
+            w = bits[p >> 5];
+            const bool hit = (w >> (p & 31)) & 1u;
+            const unsigned r = run[p];
+            run[p] = hit ? (uint8_t)min(r + 1u, 255u) : (uint8_t)0;
+        }
+        __syncwarp();                                         // every lane has read the word
+        if (valid && (p & 31) == 0 && w != 0u) bits[p >> 5] = 0u;
     }
 }
 

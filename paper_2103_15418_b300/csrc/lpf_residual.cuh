@@ -261,6 +261,7 @@ __device__ __noinline__ void emit_res_candidates(const ResArgs& ra, int row, int
     if (cand) {
         unsigned rank = __popc(bal & ((1u << lane) - 1u));
         uint64_t pix = ((uint64_t)ys << a.bx) | (uint64_t)xs;
+        mark_zero_row(a, row, pix);
         for (int m = 0; m < nm; ++m) {
             unsigned idx = base + rank * nm + m;
             if (idx < (unsigned)a.cap) {
@@ -318,6 +319,7 @@ __global__ void __launch_bounds__(256) k_lmax_res(ResArgs ra) {
         base = __shfl_sync(0xffffffffu, base, 31);
         if (cand) {
             const uint64_t pix = ((uint64_t)ys << a.bx) | (uint64_t)xs;
+            mark_zero_row(a, row, pix);
             for (unsigned m = 0; m < nm; ++m) {
                 const unsigned idx = base + incl - nm + m;
                 if (idx < (unsigned)a.cap) {

@@ -51,6 +51,9 @@ int ceil_log2(int64_t v) {
     return b;
 }
 
+// words of one steady-source bit map (a bit per pixel of the key space)
+size_t steady_words(int bx, int by) { return std::max<size_t>(((size_t)1 << (bx + by)) / 32, 1); }
+
 // Candidate buffers of one push.  Consecutive pushes alternate between two
 // lanes, so that the ordering, formatting and statistics of push T (its tail,
 // on a second stream) overlap the ingest and search of push T + 1.
@@ -128,9 +131,11 @@ struct lpf_stream {
     size_t device_bytes = 0;
 
     // opt-in steady-source suppression (suppress_steady > 0): per pixel of the key
-    // space (2^(bx + by)), this push's zero-delay candidates and the run length
-    unsigned* steady_bits = nullptr; // [2^(bx+by) / 32]
+    // space (2^(bx + by)), the push's zero-delay candidates (one bit map per push
+    // lane, set by the kernels that find the candidates) and the run length
+    unsigned* steady_bits = nullptr; // [2][steady_words]
     uint8_t* steady_run = nullptr;   // [2^(bx+by)]
+    int zero_row = -1;               // the distinct delay row that is all zero, -1 if none
     // host pinned
     unsigned* h_count = nullptr;     // [slots][2]: records emitted, records dropped by the steady mask
     // quality control (App. A), when prm.qc: running per-pixel statistics of the
@@ -709,6 +714,8 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
     // used by the tail of the push two back
     LPF_TRY(cudaStreamWaitEvent(fs, L.tail_done, 0));
     lpf::k_zero_u32<<<1, 32, 0, fs>>>(L.counter, 4);   // candidates, dropped, crossings (u64 at word 2)
+    // this lane's zero-delay marks (cleared by the lane's previous run-length update)
+    unsigned* zbits = s->prm.suppress_steady > 0 ? s->steady_bits + p * steady_words(s->bx, s->by) : nullptr;
     prof_begin(s, sl, ST_FILTER, fs);
     lpf::FilterArgs a;
     if (n_rows > 0) {
@@ -717,6 +724,7 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
         a.member_start = s->d_member_start; a.member_ord = s->d_member_ord;
         a.keys = L.keys[0]; a.vals = L.vals[0]; a.counter = L.counter; a.cap = s->prm.cand_cap;
         a.bx = s->bx; a.by = s->by; a.partials = L.partials;
+        a.zbits = zbits; a.zrow = s->zero_row;
         if (clip) {
             lpf::k_clip_emit<<<dim3((unsigned)n_filter_blocks(s), (unsigned)ca.F), 256, 0, s->st>>>(
                 ca, a, s->prm.lmax_r);
@@ -756,11 +764,8 @@ int enqueue_push(lpf_stream* s, const float* frame_dev, int64_t T) {
     if (s->prm.suppress_steady > 0) {
         const int shift = s->bx + s->by;
         const int64_t npix = (int64_t)1 << shift;
-        LPF_TRY(cudaMemsetAsync(s->steady_bits, 0, (size_t)(npix + 31) / 32 * sizeof(unsigned), ts));
-        lpf::k_steady_mark<<<kSortBlocks, lpf::kOrdThreads, 0, ts>>>(L.keys[0], L.counter, s->prm.cand_cap, shift,
-                                                                     s->d_ord2d, s->d_dmax, s->steady_bits);
         lpf::k_steady_update<<<(unsigned)std::min<int64_t>((npix + 255) / 256, 148 * 16), 256, 0, ts>>>(
-            s->steady_bits, s->steady_run, npix);
+            zbits, s->steady_run, npix);
         lpf::k_steady_apply<<<kSortBlocks, lpf::kOrdThreads, 0, ts>>>(L.keys[0], L.counter, s->prm.cand_cap, shift,
                                                                       s->d_ord2d, s->d_dmax, s->steady_run,
                                                                       s->prm.suppress_steady, L.counter + 1);
@@ -929,6 +934,8 @@ int plan_stream(lpf_stream** out, int H, int W, int F, const double* freqs_mhz, 
     }
     s->bx = std::max(1, ceil_log2(W));
     s->by = std::max(1, ceil_log2(H));
+    for (int rr = 0; rr < s->n_distinct && !band; ++rr)
+        if (s->row_dmax[rr] == 0) s->zero_row = rr;      // max delay 0: every delay is 0
     s->bo = std::max(1, ceil_log2(s->n_dm));
     s->key_bits = s->bx + s->by + s->bo;
     if (s->key_bits > 64) {
@@ -995,7 +1002,7 @@ size_t footprint_bytes(const lpf_stream* s) {
     t += (size_t)s->n_slots * (b(cap * sizeof(lpf::CandidateRec)) + b(nd * 3 * 8));
     if (s->prm.suppress_steady > 0) {
         const size_t npix = (size_t)1 << (s->bx + s->by);
-        t += b(npix / 8) + b(npix);
+        t += b(2 * steady_words(s->bx, s->by) * 4) + b(npix);
     }
     return t;
 }
@@ -1101,10 +1108,13 @@ int lpf_stream_open(lpf_stream** out, int H, int W, int F, const double* freqs_m
     }
     if (rc == LPF_OK && prm.suppress_steady > 0) {
         const size_t npix = (size_t)1 << (s->bx + s->by);
-        rc = dev_alloc(s, &s->steady_bits, std::max<size_t>(npix / 32, 1));
+        rc = dev_alloc(s, &s->steady_bits, 2 * steady_words(s->bx, s->by));
         if (rc == LPF_OK) rc = dev_alloc(s, &s->steady_run, npix);
-        // no pixel has a run yet
-        if (rc == LPF_OK && cudaMemsetAsync(s->steady_run, 0, npix, s->st) != cudaSuccess) rc = LPF_E_CUDA;
+        // no pixel has a run yet, no lane a mark
+        if (rc == LPF_OK && (cudaMemsetAsync(s->steady_run, 0, npix, s->st) != cudaSuccess ||
+                             cudaMemsetAsync(s->steady_bits, 0, 2 * steady_words(s->bx, s->by) * sizeof(unsigned),
+                                             s->st) != cudaSuccess))
+            rc = LPF_E_CUDA;
     }
     for (int i = 0; i < s->n_slots && rc == LPF_OK; ++i) {
         rc = dev_alloc(s, &s->slots[i].d_out, (size_t)prm.cand_cap);

@@ -249,8 +249,9 @@ def test_cnn_arguments_are_checked_before_any_cuda_call():
 
 
 def test_steady_suppression_arguments_and_footprint():
-    """suppress_steady: 0..255, dispersed search only; its state is one bit and one
-    byte per pixel of the 2^(bx + by) key space, planned without a GPU."""
+    """suppress_steady: 0..255, dispersed search only; its state is one bit per
+    pixel of the 2^(bx + by) key space for each of the two push lanes and one byte
+    per pixel, planned without a GPU."""
     import synth
     lib = lpf
     spec = synth.spec_tiny()
@@ -258,7 +259,7 @@ def test_steady_suppression_arguments_and_footprint():
                                     box_r=spec.box_r, **kw)
     npix = 1 << (2 * int(np.ceil(np.log2(spec.W))))          # 64 x 64: 6 + 6 key bits
     assert spec.H == spec.W == 64
-    assert fp(suppress_steady=3) - fp() == npix // 8 + npix
+    assert fp(suppress_steady=3) - fp() == 2 * (npix // 8) + npix
     assert fp(suppress_steady=255) == fp(suppress_steady=1)
     for bad in (-1, 256):
         with pytest.raises(lib.LpfError):

@@ -126,3 +126,37 @@ def test_footprint_matches_allocation(lib):
         fp = lib.footprint(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth, **kw(sp))
         with lib.Stream(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth, **kw(sp)) as s:
             assert s.info()["device_bytes"] == fp
+
+
+def test_served_suppression_with_a_full_list_matches_direct(lib):
+    """A stream with steady-source suppression and a 50-record candidate list,
+    served and direct.  Frames that fit the list give the same records and count;
+    which records an overflowed list holds is unspecified, so for those frames n_found
+    is the number of sorted records returned.  The mask state does not depend on
+    the list, so frames after an overflow agree again."""
+    from tests.parity import assert_sorted_unique
+    sp = synth.spec_tiny(kappa=4.0)
+    st = synth.SyntheticStream(sp, seed=3)
+    cap = 50
+    opts = dict(kappa=sp.kappa, box_r=sp.box_r, suppress_steady=2, cand_cap=cap)
+    n = 12
+    direct = {}
+    with lib.Stream(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth, **opts) as s:
+        for T in range(n):
+            s.push(torch.from_numpy(st.frame(T)).cuda(), T)
+            Tp, c, nf, trunc = s.poll(timeout_ms=60000)
+            direct[Tp] = (c.tobytes(), nf, trunc)
+    flags = [v[2] for v in direct.values()]
+    assert any(flags) and not all(flags)
+    with lib.Server(8 << 30, max_streams=2) as srv:
+        sid = srv.open_stream(sp.H, sp.W, sp.freqs_mhz, sp.dm_grid, sp.depth, **opts)
+        for T in range(n):
+            assert srv.submit(sid, st.frame(T), T) == lib.LPF_OK
+            Tp, c, nf, _ = srv.fetch(sid, timeout_ms=60000)
+            assert Tp == T
+            if direct[T][2]:
+                assert_sorted_unique(c)
+                assert nf == len(c) <= cap, T
+            else:
+                assert (c.tobytes(), nf) == direct[T][:2], T
+        srv.close_stream(sid)
