@@ -120,3 +120,33 @@ def test_steady_suppression_on_the_tiled_path_and_with_a_full_list(lib):
             else:
                 assert not trunc_s and set(got_s) == want and ns == len(want), T
     assert saw_trunc and saw_drop
+
+
+def test_steady_suppression_on_the_clipping_path(lib):
+    """The marks set by the clipping emit (dispersed search, two clipping
+    iterations): per push, the suppressed stream's candidates are the unsuppressed
+    clipping stream's candidates after the oracle's mask and drop rule."""
+    spec = synth.spec_tiny(kappa=4.0)
+    st = synth.SyntheticStream(spec, seed=3)
+    delays = O.delay_table(spec.freqs_mhz, spec.dm_grid, spec.cadence_s)
+    dmax = delays.max(axis=1)
+    K = 2
+    mask = O.SteadyMask(K)
+    kw = dict(kappa=spec.kappa, box_r=spec.box_r, clip_iters=2)
+    dropped = 0
+    with lib.Stream(spec.H, spec.W, spec.freqs_mhz, spec.dm_grid, spec.depth, suppress_steady=K, **kw) as s, \
+         lib.Stream(spec.H, spec.W, spec.freqs_mhz, spec.dm_grid, spec.depth, **kw) as s0:
+        for T in range(10):
+            x = torch.from_numpy(st.frame(T)).cuda()
+            s.push(x, T)
+            s0.push(x, T)
+            _, c, n, trunc = s.poll(timeout_ms=60000)
+            _, c0, n0, _ = s0.poll(timeout_ms=60000)
+            assert not trunc and n == len(c)
+            assert_sorted_unique(c)
+            got, all0 = _keys(c), _keys(c0)
+            steady = mask.update({(k[2], k[3]) for k in all0 if dmax[k[1]] == 0})
+            want = {r[:4]: r[4] for r in O.suppress_steady([k + (v,) for k, v in all0.items()], dmax, steady)}
+            assert got == want, (T, set(got) ^ set(want))
+            dropped += n0 - n
+    assert dropped > 0
