@@ -100,22 +100,31 @@ def workload_spec(dtype):
 FILTER_OPS_PER_PIXEL_TRIAL = 11
 
 
-def kernel_traffic(field="dram_bytes_per_launch"):
-    """A per-launch counter (DRAM bytes, or executed warp instructions) from the
-    committed ncu capture, or None where the kernel's source has changed since the
-    counters were taken or the capture has no such counter."""
+def sources_sha256(sources):
+    """SHA-256 of the files a kernel is compiled from (one path or a list, read in
+    order and hashed as one byte string), relative to the repository root."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    h = hashlib.sha256()
+    for src in [sources] if isinstance(sources, str) else sources:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def kernel_traffic(field="dram_bytes_per_launch", path=None):
+    """A per-launch counter (DRAM bytes, or executed warp instructions) from the
+    committed ncu capture, or None where a source of the kernel has changed since
+    the counters were taken or the capture has no such counter."""
+    path = path or os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))
     except Exception:
         return {}
     out = {}
     for k, v in rec.items():
-        src = os.path.join(ROOT, v["source"])
         try:
-            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        except Exception:
+            sha = sources_sha256(v["source"])
+        except OSError:
             continue
         out[k] = v.get(field) if sha == v["sha256"] else None
     return out
@@ -492,6 +501,8 @@ def run_ours(args):
     sm_mhz = peaks.get("sm_max_mhz", 2032.0)
     alu_peak = sms * 128 * sm_mhz * 1e6 / 1e12          # one FP32 op per lane per clock
     traffic = kernel_traffic()
+    # the committed captures: per storage type for the shift-sum, FP32 and FP16 for the filter
+    fkey = "k_filter_res" if args.dtype == "fp32" else "k_filter_res_" + args.dtype
     HW = spec.H * spec.W
     nd = info["n_distinct"]
     nb = algorithmic_bytes(spec, delays, args.dtype)
@@ -509,11 +520,11 @@ def run_ours(args):
     roof_f = {"kernel": "k_filter_res<15> (box spread, S/N, threshold, stats)", "bound": "alu",
               "achieved": f_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": f_ach / alu_peak,
               "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
-              "traffic": traffic.get("k_filter_res"),
+              "traffic": traffic.get(fkey),
               "algorithmic_flop_per_launch": f_ops, "avg_launch_ms": f_ms, "launches_per_step": 1}
     # the filter is bound by instruction issue: executed warp instructions per launch
     # (ncu) over the event-timed launch, against 4 schedulers per SM at the clock
-    f_inst = kernel_traffic("warp_inst_per_launch").get("k_filter_res")
+    f_inst = kernel_traffic("warp_inst_per_launch").get(fkey)
     issue_peak = sms * 4 * sm_mhz * 1e6 / 1e12
     roof_f_issue = {"kernel": "k_filter_res<15> (instruction issue)", "bound": "issue",
                     "achieved": f_inst / (f_ms / 1e3) / 1e12 if f_inst else None, "peak": issue_peak,
@@ -522,7 +533,7 @@ def run_ours(args):
                     "peak_source": f"{sms} SMs x 4 schedulers x {sm_mhz:.0f} MHz",
                     "warp_instructions_per_launch": f_inst, "avg_launch_ms": f_ms}
     step_traffic = None
-    tr_keys = ["k_dedisperse_" + args.dtype, "k_filter_res"]
+    tr_keys = ["k_dedisperse_" + args.dtype, fkey]
     if all(traffic.get(k) for k in tr_keys):
         # DRAM bytes of the main-stream kernels that move the bulk (ncu, one launch each)
         step_traffic = sum(traffic[k] for k in tr_keys)
@@ -575,8 +586,7 @@ def run_ours(args):
                                       "frames in flight"}
     if f16 is not None:
         sp16 = workload_spec("fp16")
-        # the filter reads the same FP32 R images at either storage type
-        tr16 = ["k_dedisperse_fp16", "k_filter_res"]
+        tr16 = ["k_dedisperse_fp16", "k_filter_res_fp16"]
         traffic16 = sum(traffic[k] for k in tr16) if all(traffic.get(k) for k in tr16) else None
         ms16 = 1e3 * f16["elapsed"] / args.steps
         line["fp16"] = {"storage": "fp16", "ms_per_step": ms16, "value": pix_dm * args.steps * ws / f16["elapsed"],

@@ -63,3 +63,21 @@ def test_clock_summary_median_reasons_and_window():
     for k in (c, c2):                                        # the unused sample files
         k.f.close()
         os.unlink(k.f.name)
+
+
+def test_kernel_traffic_goes_stale_with_any_source(tmp_path):
+    """A capture's counters are used only while every file its kernel is compiled
+    from is unchanged (hashed together, in order)."""
+    srcs = ["paper_2103_15418_b300/csrc/lpf_dedisperse.cuh", "paper_2103_15418_b300/csrc/lpf_kernels.cuh"]
+    rec = {"a": {"dram_bytes_per_launch": 7, "source": srcs, "sha256": bench.sources_sha256(srcs)},
+           "b": {"dram_bytes_per_launch": 8, "source": srcs[0], "sha256": bench.sources_sha256(srcs[:1])},
+           "c": {"dram_bytes_per_launch": 9, "source": srcs[::-1], "sha256": bench.sources_sha256(srcs)}}
+    import json
+    p = tmp_path / "traffic.json"
+    p.write_text(json.dumps(rec))
+    got = bench.kernel_traffic(path=str(p))
+    assert got == {"a": 7, "b": 8, "c": None}
+    # the committed record: every kernel's sources exist and the hashes are well formed
+    committed = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
+    for k, v in committed.items():
+        assert len(v["sha256"]) == 64 and bench.sources_sha256(v["source"]), k
